@@ -1,0 +1,214 @@
+/*
+ * blr.h -- C ABI of the GB300 tiled Householder BLR-QR library (libblrqr.so).
+ *
+ * Method: Apriansyah & Yokota, "Parallel QR Factorization of Block Low-Rank
+ * Matrices".  A (m x n, m >= n) is tiled into p x q square tiles of size b
+ * (p = m/b, q = n/b, Section 2); each tile is dense or U V^T with U
+ * orthonormal (Eq. 7, Section 3.1).  blr_qr computes the tiled Householder
+ * factorization of Algorithm 4 with the BLR tile kernels of Section 3.4, so
+ * that A~ = Q R with Q stored as compact-WY reflectors (Eq. 3, Eq. 21).
+ *
+ * Conventions for every entry point:
+ *  - Matrices are column-major doubles.  "device" pointers are CUDA device
+ *    memory of the current device, "host" pointers are ordinary host memory.
+ *  - Every call returns an int status: BLR_OK (0) or one of the BLR_ERR_*
+ *    codes below; blr_last_error() gives a message for the calling thread.
+ *  - Calls are ordered on the given stream (cudaStream_t passed as void*,
+ *    NULL = legacy default stream) and return after the work has finished,
+ *    because each reads back a device status word.
+ *  - Handles (blr_matrix, blr_factor) own device memory allocated by the
+ *    library; the caller owns every buffer it passes in.
+ *  - Nothing here falls back to the CPU: without a usable CUDA device every
+ *    call fails with BLR_ERR_CUDA.
+ */
+#ifndef BLR_H
+#define BLR_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define BLR_OK 0
+#define BLR_ERR_INVALID 1        /* bad sizes, pointers or options */
+#define BLR_ERR_OOM 2            /* device allocation failed */
+#define BLR_ERR_CUDA 3           /* a CUDA runtime call failed */
+#define BLR_ERR_TIMEOUT 4        /* the device scheduler made no progress within its budget */
+#define BLR_ERR_NUMERIC 5        /* NaN/Inf met, or a zero pivot in a triangular solve */
+#define BLR_ERR_RANK_OVERFLOW 6  /* a rank exceeded the tile's factor capacity */
+
+#define BLR_PREC_FP64 0          /* every step in FP64 */
+#define BLR_PREC_MIXED 1         /* trailing updates and recompression in FP32; panels FP64 */
+
+#define BLR_KERNEL_INV1D 0       /* 1/(|x-y| + 1e-3), 1D points */
+#define BLR_KERNEL_YUKAWA3D 1    /* exp(-r)/(r + 1e-3), 3D points */
+#define BLR_KERNEL_LAPLACE3D 2   /* 1/(r + 1e-3), 3D points */
+
+typedef struct blr_matrix blr_matrix; /* opaque BLR matrix (device tiles + ranks) */
+typedef struct blr_factor blr_factor; /* opaque factor: in-place R/Y~ tiles + T panels */
+
+/*
+ * Options.  Zero-initialise, then set what you need (blr_opts_default fills
+ * the defaults).
+ *  b            tile size; a multiple of 32 in [32, 1024]; m and n must be
+ *               multiples of b (Section 2 tiling).
+ *  tol          compression tolerance: per tile, the smallest rank r with
+ *               ||A_ij - U V^T||_F <= tol ||A_ij||_F (Section 3.1), found by
+ *               truncated pivoted QR; ignored when fixed_rank > 0.
+ *  fixed_rank   > 0: every off-diagonal tile is its best rank-fixed_rank
+ *               approximation (truncated SVD).
+ *  rec_tol      relative tolerance of the rounded additions (Algorithm 6)
+ *               inside blr_qr; 0 means "use tol".
+ *  dense_rank   a low-rank tile whose rank would exceed this is stored
+ *               dense (Section 3.1 fallback); 0 means b/2, the maximum.
+ *  precision    BLR_PREC_FP64 or BLR_PREC_MIXED.
+ *  sched_ctas   persistent scheduler CTAs; 0 = one per SM.
+ *  watchdog_ms  the scheduler gives up (BLR_ERR_TIMEOUT) after this many
+ *               milliseconds without any task completing; 0 = 20000.
+ */
+typedef struct blr_opts {
+  int b;
+  int fixed_rank;
+  double tol;
+  double rec_tol;
+  int dense_rank;
+  int precision;
+  int sched_ctas;
+  int watchdog_ms;
+  int reserved[8];
+} blr_opts;
+
+/* Statistics of a handle (host struct filled by blr_stats). */
+typedef struct blr_stats_t {
+  int m, n, b, p, q;
+  int n_dense;              /* dense tiles (diagonal included) */
+  int max_rank;             /* largest low-rank tile rank */
+  double mean_rank;         /* mean rank over low-rank tiles */
+  long long device_bytes;   /* device memory held by the handle */
+  double flops[5];          /* factor only: counted FP ops per task type
+                               (GEQRT, LARFB, TSQRT, TPMQRT, total) */
+  long long tasks[4];       /* factor only: tasks executed per type */
+  double seconds;           /* factor only: device time of the last blr_qr */
+} blr_stats_t;
+
+/* Fills *opts with the defaults (b = 512, tol = 1e-8, FP64). */
+void blr_opts_default(blr_opts* opts);
+
+/* Message of the last failing call on this thread ("" if none). */
+const char* blr_last_error(void);
+
+/*
+ * blr_compress_kernel -- build the BLR matrix of a kernel matrix
+ * A(i,j) = K(|x_i - y_j|) * col_scale[j] (Section 3.1, Eq. 7) on the device.
+ *  x_host      host, dim x m (column i = point x_i), already ordered.
+ *  y_host      host, dim x n.
+ *  dim         1 or 3 (must match kernel_id).
+ *  col_scale   host, n doubles, or NULL for no scaling.
+ *  kernel_id   BLR_KERNEL_*.
+ * Diagonal tiles (i == j) are dense (weak admissibility); every other tile
+ * is compressed per opts (tol or fixed_rank) and kept dense when its rank
+ * exceeds the dense threshold.  *out receives a new handle.
+ * Errors: BLR_ERR_INVALID (m < n, sizes not multiples of b, bad dim/kernel),
+ * BLR_ERR_OOM, BLR_ERR_CUDA.
+ */
+int blr_compress_kernel(const double* x_host, const double* y_host, int dim, int m, int n,
+                        int kernel_id, const double* col_scale, const blr_opts* opts,
+                        blr_matrix** out, void* stream);
+
+/*
+ * blr_compress_dense -- BLR matrix of a dense device matrix A (m x n,
+ * leading dimension lda >= m), compressed as in blr_compress_kernel.
+ * A is only read.  Errors as above.
+ */
+int blr_compress_dense(const double* a_dev, int lda, int m, int n, const blr_opts* opts,
+                       blr_matrix** out, void* stream);
+
+/*
+ * blr_matrix_import -- BLR matrix from explicit host tiles in the library's
+ * layout: tiles_host holds p*q blocks of b*b doubles, block (i,j) at offset
+ * (j*p + i)*b*b; a dense tile is b x b column-major; a low-rank tile of
+ * rank r stores U (b x r, orthonormal columns) in its first b*r doubles and
+ * V (b x r) from offset b*(b/2).  ranks_host[(j*p)+i] is r, or -1 for dense.
+ * Errors: BLR_ERR_INVALID (rank > b/2), BLR_ERR_OOM, BLR_ERR_CUDA.
+ */
+int blr_matrix_import(int m, int n, int b, const int* ranks_host, const double* tiles_host,
+                      blr_matrix** out, void* stream);
+
+/*
+ * blr_matrix_export -- copy tiles and ranks of a matrix, or of a factor's
+ * in-place storage, to host buffers of p*q*b*b doubles and p*q ints (same
+ * layout as blr_matrix_import).  handle_is_factor selects the handle type.
+ */
+int blr_matrix_export(const void* handle, int handle_is_factor, int* ranks_host,
+                      double* tiles_host, void* stream);
+
+/* Deep copy of a BLR matrix (e.g. to keep A~ for refinement). */
+int blr_matrix_clone(const blr_matrix* a, blr_matrix** out, void* stream);
+
+/*
+ * blr_qr -- tiled Householder BLR-QR (Algorithm 4 with Section 3.4's
+ * GEQRT / apply-block-reflector / update-QR / apply-trapezoidal-reflector,
+ * rounded additions of Algorithm 6), run as one persistent device-side task
+ * scheduler over the tile DAG (Section 4.3).
+ *  a       consumed: its tiles become the factor's in-place storage and the
+ *          handle is invalidated (do not use or destroy it afterwards; the
+ *          factor owns the memory).  Clone it first to keep A~.
+ *  opts    rec_tol, dense_rank, precision, sched_ctas, watchdog_ms are used.
+ *  f       receives the factor.  Tile (k,k) holds R_kk (upper) and Y_kk
+ *          (strictly lower, unit diagonal implied); tile (k,j), j > k, holds
+ *          R_kj; tile (i,k), i > k, holds Y~_ik = U_ik Y_ik (low-rank: U slot
+ *          = U_ik, V slot = Y_ik^T) or a dense Y_ik.
+ * Errors: BLR_ERR_INVALID, BLR_ERR_OOM, BLR_ERR_CUDA, BLR_ERR_TIMEOUT,
+ * BLR_ERR_NUMERIC (NaN/Inf in a reflector), BLR_ERR_RANK_OVERFLOW.  On error
+ * the factor is not created and the consumed matrix is freed.
+ */
+int blr_qr(blr_matrix* a, const blr_opts* opts, blr_factor** f, void* stream);
+
+/*
+ * blr_apply_qt -- in place on a device matrix B (m x nrhs, ldb >= m):
+ * trans = 0: B <- Q^T B (reflectors in factorization order);
+ * trans = 1: B <- Q B (reverse order; Algorithm 5 read with the "I -" of
+ * Eq. 21's reflector).  Exact application of the stored reflectors.
+ */
+int blr_apply_qt(const blr_factor* f, double* b_dev, int ldb, int nrhs, int trans,
+                 void* stream);
+
+/*
+ * blr_lstsq -- least squares min ||A~ X - B||_F via the factor (QR used for
+ * least squares, Section 1): X = R^{-1} (Q^T B)(1:n), then refine_steps
+ * steps of X += R^{-1} Q_1^T (B - A X) with A = a_orig (BLR, FP64).
+ *  b_dev   device, m x nrhs (ldb), read only.   x_dev  device, n x nrhs (ldx).
+ *  a_orig  may be NULL when refine_steps == 0.
+ * Errors: BLR_ERR_NUMERIC for a zero or non-finite diagonal of R.
+ */
+int blr_lstsq(const blr_factor* f, const blr_matrix* a_orig, const double* b_dev, int ldb,
+              double* x_dev, int ldx, int nrhs, int refine_steps, void* stream);
+
+/* Y = A~ X for a BLR matrix (X device n x nrhs, Y device m x nrhs). */
+int blr_matmul(const blr_matrix* a, const double* x_dev, int ldx, double* y_dev, int ldy,
+               int nrhs, void* stream);
+
+/* Y = R X for the factor's n x n upper triangular BLR R (X, Y device n x nrhs). */
+int blr_apply_r(const blr_factor* f, const double* x_dev, int ldx, double* y_dev, int ldy,
+                int nrhs, void* stream);
+
+/*
+ * blr_factor_export_t -- copy the compact-WY T panels to the host.  For the
+ * reflector block of tile (i,k) (i >= k) the library stores T_ik as b/32
+ * diagonal 32 x 32 upper-triangular blocks (inner blocking, each the T of 32
+ * consecutive reflectors), laid out 32 x b column-major; blocks appear in
+ * column-major order of (i,k), i = k..p-1 for each k.  t_host holds
+ * (sum_k (p-k)) * 32 * b doubles.
+ */
+int blr_factor_export_t(const blr_factor* f, double* t_host, void* stream);
+
+/* Statistics of a matrix or factor handle. */
+int blr_stats(const void* handle, int handle_is_factor, blr_stats_t* out);
+
+void blr_destroy_matrix(blr_matrix* a);
+void blr_destroy_factor(blr_factor* f);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BLR_H */

@@ -1,0 +1,803 @@
+// CTA-collective FP64 building blocks of the BLR-QR kernels.
+//
+// Every routine is called by all BLR_NT threads of a CTA, starts and ends
+// with a barrier, and works on column-major matrices (element (r,c) at
+// p[r + c*ld]).  Global operands that other CTAs may have written during a
+// persistent launch are read with ld.global.cg (L2, never a stale L1 line);
+// CTA-private scratch and shared memory are read with plain loads.
+//
+// Householder convention (LAPACK's): for x = [alpha; x2], beta =
+// -sign(alpha) ||x|| (sign(0) = +1), tau = (beta - alpha)/beta,
+// v = [1; x2/(alpha - beta)], so (I - tau v v^T) x = beta e_1; a zero tail
+// gives tau = 0.  Blocks of BLR_NB reflectors are kept in compact-WY form
+// I - Y T Y^T (Eq. 3), T built by the Schreiber-Van Loan recurrence.
+#pragma once
+#include "blr_internal.h"
+
+#define FULLMASK 0xffffffffu
+
+namespace {
+
+__device__ __forceinline__ double ldg(const double* p) { return __ldcg(p); }
+
+// Shared-memory carve-out.
+struct Sm {
+  double* pnl;   // BLR_SM_PNL
+  double* cs;    // staged block
+  double* z;     // NB x CW
+  double* w;     // NB x CW
+  double* t;     // NB x NB
+  double* rp;    // NB x NB
+  double* red;   // 8
+  double* scal;  // 8
+  double* tau;   // 32
+  double* vec;   // 512
+  int* ivec;     // 512 ints
+  int* flag;     // 4 ints
+};
+
+struct Ctx {
+  Sm s;
+  int* status;      // global status word
+  double fma;       // fused multiply-adds counted for the current task (same on all threads)
+};
+
+__device__ __forceinline__ Sm sm_carve(double* base) {
+  Sm s;
+  s.pnl = base;
+  s.cs = s.pnl + BLR_SM_PNL;
+  s.z = s.cs + BLR_SM_CS;
+  s.w = s.z + BLR_SM_Z;
+  s.t = s.w + BLR_SM_W;
+  s.rp = s.t + BLR_SM_T;
+  double* m = s.rp + BLR_SM_RP;
+  s.red = m;
+  s.scal = m + 8;
+  s.tau = m + 16;
+  s.vec = m + 48;
+  s.ivec = reinterpret_cast<int*>(m + 48 + 512);
+  s.flag = reinterpret_cast<int*>(m + 48 + 512 + 256);
+  return s;
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(FULLMASK, v, o);
+  return v;
+}
+
+// Sum over the CTA; every thread gets the same value.
+__device__ __forceinline__ double block_sum(double v, double* red) {
+  v = warp_sum(v);
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  double s = 0.0;
+#pragma unroll
+  for (int i = 0; i < BLR_NWARP; i++) s += red[i];
+  return s;
+}
+
+__device__ __forceinline__ void house(double alpha, double sig2, double& beta, double& tau,
+                                      double& scale) {
+  if (sig2 == 0.0) {
+    beta = alpha;
+    tau = 0.0;
+    scale = 0.0;
+    return;
+  }
+  double nrm = sqrt(alpha * alpha + sig2);
+  beta = (alpha >= 0.0) ? -nrm : nrm;
+  tau = (beta - alpha) / beta;
+  scale = 1.0 / (alpha - beta);
+}
+
+__device__ __forceinline__ void flag_numeric(Ctx& c, double x) {
+  if (!isfinite(x)) atomicOr(c.status, ST_NUMERIC);
+}
+
+// ---------------------------------------------------------------------------
+// Staging between global views and shared memory.
+// A strided view: element (r,c) at p[r*sr + c*sc].
+// ---------------------------------------------------------------------------
+struct View {
+  double* p;
+  long long sr, sc;
+  __device__ __forceinline__ double* at(int r, int c) const { return p + r * sr + c * sc; }
+};
+
+__device__ __forceinline__ View colmajor(double* p, int ld) { return View{p, 1, (long long)ld}; }
+__device__ __forceinline__ View rowmajor(double* p, int ld) { return View{p, (long long)ld, 1}; }
+
+// dst (smem, column-major ldd) = src (rows x cols); coalesced along src's unit stride.
+__device__ void stage_in(double* dst, int ldd, View src, int rows, int cols) {
+  int tot = rows * cols;
+  if (src.sr == 1) {
+    for (int e = threadIdx.x; e < tot; e += BLR_NT) {
+      int r = e % rows, c = e / rows;
+      dst[r + c * ldd] = ldg(src.at(r, c));
+    }
+  } else {
+    for (int e = threadIdx.x; e < tot; e += BLR_NT) {
+      int c = e % cols, r = e / cols;
+      dst[r + c * ldd] = ldg(src.at(r, c));
+    }
+  }
+}
+
+__device__ void stage_out(View dst, const double* src, int lds, int rows, int cols) {
+  int tot = rows * cols;
+  if (dst.sr == 1) {
+    for (int e = threadIdx.x; e < tot; e += BLR_NT) {
+      int r = e % rows, c = e / rows;
+      *dst.at(r, c) = src[r + c * lds];
+    }
+  } else {
+    for (int e = threadIdx.x; e < tot; e += BLR_NT) {
+      int c = e % cols, r = e / cols;
+      *dst.at(r, c) = src[r + c * lds];
+    }
+  }
+}
+
+// Global-to-global copy / zero of a rows x cols block (column-major both).
+__device__ void copy_mat(double* dst, int ldd, const double* src, int lds, int rows, int cols) {
+  long long tot = (long long)rows * cols;
+  for (long long e = threadIdx.x; e < tot; e += BLR_NT) {
+    int r = (int)(e % rows), c = (int)(e / rows);
+    dst[r + (long long)c * ldd] = ldg(src + r + (long long)c * lds);
+  }
+}
+
+__device__ void zero_mat(double* dst, int ldd, int rows, int cols) {
+  long long tot = (long long)rows * cols;
+  for (long long e = threadIdx.x; e < tot; e += BLR_NT) {
+    int r = (int)(e % rows), c = (int)(e / rows);
+    dst[r + (long long)c * ldd] = 0.0;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Unblocked Householder QR of a panel held in shared memory (h x w, w <= 32):
+// R in the upper triangle, v_j below the diagonal, tau[j].
+// ---------------------------------------------------------------------------
+__device__ void panel_qr(double* P, int ldp, int h, int w, double* tau, Ctx& c) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  __syncthreads();
+  for (int j = 0; j < w && j < h; j++) {
+    double part = 0.0;
+    for (int r = j + 1 + threadIdx.x; r < h; r += BLR_NT) {
+      double x = P[r + j * ldp];
+      part += x * x;
+    }
+    double sig2 = block_sum(part, c.s.red);
+    if (threadIdx.x == 0) {
+      double beta, tj, sc;
+      house(P[j + j * ldp], sig2, beta, tj, sc);
+      flag_numeric(c, beta);
+      c.s.scal[0] = beta;
+      c.s.scal[1] = tj;
+      c.s.scal[2] = sc;
+    }
+    __syncthreads();
+    const double tj = c.s.scal[1], sc = c.s.scal[2];
+    for (int r = j + 1 + threadIdx.x; r < h; r += BLR_NT) P[r + j * ldp] *= sc;
+    __syncthreads();
+    for (int l = j + 1 + warp; l < w; l += BLR_NWARP) {
+      double acc = 0.0;
+      for (int r = j + 1 + lane; r < h; r += 32) acc += P[r + j * ldp] * P[r + l * ldp];
+      acc = warp_sum(acc);
+      double wl = (__shfl_sync(FULLMASK, P[j + l * ldp], 0) + acc) * tj;
+      if (lane == 0) P[j + l * ldp] -= wl;
+      for (int r = j + 1 + lane; r < h; r += 32) P[r + l * ldp] -= wl * P[r + j * ldp];
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      P[j + j * ldp] = c.s.scal[0];
+      tau[j] = tj;
+    }
+    __syncthreads();
+  }
+  // zero tau for columns beyond h (cannot happen for m >= n callers)
+  for (int j = h + threadIdx.x; j < w; j += BLR_NT) tau[j] = 0.0;
+  __syncthreads();
+  double hw = (double)h * w - 0.5 * (double)w * w;
+  c.fma += 2.0 * hw * w * 0.5 + hw;
+}
+
+// T (w x w upper, ld NB) from the Gram matrix G of the reflector vectors
+// (G[a + l*NB] for a < l) and tau: T_jj = tau_j, T(0:j,j) = -tau_j T(0:j,0:j) G(0:j,j).
+__device__ void t_recur(const double* G, const double* tau, int w, double* T, Ctx& c) {
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    const int a = threadIdx.x;
+    for (int j = 0; j < BLR_NB; j++) {
+      double v = 0.0;
+      if (j < w) {
+        if (a < j) {
+          double s = 0.0;
+          for (int cc = a; cc < j; cc++) s += T[a + cc * BLR_NB] * G[cc + j * BLR_NB];
+          v = -tau[j] * s;
+        } else if (a == j) {
+          v = tau[j];
+        }
+      }
+      T[a + j * BLR_NB] = v;
+      __syncwarp();
+    }
+  }
+  __syncthreads();
+  c.fma += (double)w * w * w / 6.0;
+}
+
+// Gram of a panel's unit-lower-trapezoidal reflectors (P from panel_qr), into G (ld NB).
+__device__ void gram_panel(const double* P, int ldp, int h, int w, double* G, Ctx& c) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  __syncthreads();
+  const int npair = w * (w - 1) / 2;
+  for (int e = warp; e < npair; e += BLR_NWARP) {
+    // decode e -> (a, l) with a < l
+    int l = 1, base = 0;
+    while (base + l <= e) { base += l; l++; }
+    int a = e - base;
+    double acc = 0.0;
+    for (int r = l + 1 + lane; r < h; r += 32) acc += P[r + a * ldp] * P[r + l * ldp];
+    acc = warp_sum(acc);
+    if (lane == 0) G[a + l * BLR_NB] = (l < h ? P[l + a * ldp] : 0.0) + acc;
+  }
+  __syncthreads();
+  c.fma += (double)h * w * w / 2.0;
+}
+
+// Gram of dense reflector blocks Bp (ry x w, ld ldb): G[a][l] = Bp(:,a).Bp(:,l).
+__device__ void gram_dense(const double* Bp, int ldb, int ry, int w, double* G, Ctx& c) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  __syncthreads();
+  const int npair = w * (w - 1) / 2;
+  for (int e = warp; e < npair; e += BLR_NWARP) {
+    int l = 1, base = 0;
+    while (base + l <= e) { base += l; l++; }
+    int a = e - base;
+    double acc = 0.0;
+    for (int r = lane; r < ry; r += 32) acc += Bp[r + a * ldb] * Bp[r + l * ldb];
+    acc = warp_sum(acc);
+    if (lane == 0) G[a + l * BLR_NB] = acc;
+  }
+  __syncthreads();
+  c.fma += (double)ry * w * w / 2.0;
+}
+
+// ---------------------------------------------------------------------------
+// C (h x nc, global, ldc) <- (I - Y T' Y^T) C with Y the unit lower
+// trapezoidal reflectors of a panel in shared memory (P, ldp, h x w) and
+// T' = T^T (trans, applies Q^T) or T (applies Q).
+// ---------------------------------------------------------------------------
+__device__ void apply_refl_panel(double* C, long long ldc, int h, int nc, const double* P, int ldp,
+                                 int w, const double* T, bool trans, Ctx& c) {
+  const int a = threadIdx.x & 31, grp = threadIdx.x >> 5;
+  double* Cs = c.s.cs;
+  const int ldcs = BLR_RB + 1;
+  double* Z = c.s.z;
+  double* W = c.s.w;
+  for (int c0 = 0; c0 < nc; c0 += BLR_CW) {
+    const int cw = min(BLR_CW, nc - c0);
+    double acc[BLR_CW / BLR_NWARP];
+#pragma unroll
+    for (int k = 0; k < BLR_CW / BLR_NWARP; k++) acc[k] = 0.0;
+    for (int r0 = 0; r0 < h; r0 += BLR_RB) {
+      const int rb = min(BLR_RB, h - r0);
+      __syncthreads();
+      for (int e = threadIdx.x; e < rb * cw; e += BLR_NT) {
+        int rr = e % rb, ll = e / rb;
+        Cs[rr + ll * ldcs] = ldg(C + (r0 + rr) + (long long)(c0 + ll) * ldc);
+      }
+      __syncthreads();
+      if (a < w) {
+        for (int rr = 0; rr < rb; rr++) {
+          const int row = r0 + rr;
+          const double y = (row > a) ? P[row + a * ldp] : (row == a ? 1.0 : 0.0);
+#pragma unroll
+          for (int k = 0; k < BLR_CW / BLR_NWARP; k++) {
+            int ll = grp + BLR_NWARP * k;
+            if (ll < cw) acc[k] += y * Cs[rr + ll * ldcs];
+          }
+        }
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < BLR_CW / BLR_NWARP; k++) {
+      int ll = grp + BLR_NWARP * k;
+      if (a < BLR_NB && ll < BLR_CW) Z[a + ll * BLR_NB] = (a < w && ll < cw) ? acc[k] : 0.0;
+    }
+    __syncthreads();
+    // W = T^T Z (trans) or T Z
+#pragma unroll
+    for (int k = 0; k < BLR_CW / BLR_NWARP; k++) {
+      int ll = grp + BLR_NWARP * k;
+      if (ll < cw && a < w) {
+        double s = 0.0;
+        if (trans) {
+          for (int cc = 0; cc <= a; cc++) s += T[cc + a * BLR_NB] * Z[cc + ll * BLR_NB];
+        } else {
+          for (int cc = a; cc < w; cc++) s += T[a + cc * BLR_NB] * Z[cc + ll * BLR_NB];
+        }
+        W[a + ll * BLR_NB] = s;
+      }
+    }
+    __syncthreads();
+    // C -= Y W
+    for (long long e = threadIdx.x; e < (long long)h * cw; e += BLR_NT) {
+      int row = (int)(e % h), ll = (int)(e / h);
+      double s = 0.0;
+      const int amax = min(w, row + 1);
+      for (int aa = 0; aa < amax; aa++) {
+        const double y = (row > aa) ? P[row + aa * ldp] : 1.0;
+        s += y * W[aa + ll * BLR_NB];
+      }
+      double* cp = C + row + (long long)(c0 + ll) * ldc;
+      *cp = ldg(cp) - s;
+    }
+    __syncthreads();
+  }
+  c.fma += (2.0 * h * w + 0.5 * w * w) * nc;
+}
+
+// [Ct (w rows, ldt); Cb (ry x nc view)] <- (I - [I; Yb] T' [I; Yb]^T) [Ct; Cb]
+// for a block of reflectors [e_a; yb_a] (Yb in shared memory, ry x w, ldyb).
+__device__ void apply_refl_ts(double* Ct, long long ldt, View Cb, int ry, int nc,
+                              const double* Yb, int ldyb, int w, const double* T, bool trans,
+                              Ctx& c) {
+  const int a = threadIdx.x & 31, grp = threadIdx.x >> 5;
+  double* Cs = c.s.cs;
+  const int ldcs = BLR_RB + 1;
+  double* Z = c.s.z;
+  double* W = c.s.w;
+  for (int c0 = 0; c0 < nc; c0 += BLR_CW) {
+    const int cw = min(BLR_CW, nc - c0);
+    double acc[BLR_CW / BLR_NWARP];
+#pragma unroll
+    for (int k = 0; k < BLR_CW / BLR_NWARP; k++) {
+      int ll = grp + BLR_NWARP * k;
+      acc[k] = (a < w && ll < cw) ? ldg(Ct + a + (long long)(c0 + ll) * ldt) : 0.0;
+    }
+    for (int r0 = 0; r0 < ry; r0 += BLR_RB) {
+      const int rb = min(BLR_RB, ry - r0);
+      __syncthreads();
+      if (Cb.sr == 1) {
+        for (int e = threadIdx.x; e < rb * cw; e += BLR_NT) {
+          int rr = e % rb, ll = e / rb;
+          Cs[rr + ll * ldcs] = ldg(Cb.at(r0 + rr, c0 + ll));
+        }
+      } else {
+        for (int e = threadIdx.x; e < rb * cw; e += BLR_NT) {
+          int ll = e % cw, rr = e / cw;
+          Cs[rr + ll * ldcs] = ldg(Cb.at(r0 + rr, c0 + ll));
+        }
+      }
+      __syncthreads();
+      if (a < w) {
+        for (int rr = 0; rr < rb; rr++) {
+          const double y = Yb[(r0 + rr) + a * ldyb];
+#pragma unroll
+          for (int k = 0; k < BLR_CW / BLR_NWARP; k++) {
+            int ll = grp + BLR_NWARP * k;
+            if (ll < cw) acc[k] += y * Cs[rr + ll * ldcs];
+          }
+        }
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < BLR_CW / BLR_NWARP; k++) {
+      int ll = grp + BLR_NWARP * k;
+      if (ll < BLR_CW) Z[a + ll * BLR_NB] = (a < w && ll < cw) ? acc[k] : 0.0;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < BLR_CW / BLR_NWARP; k++) {
+      int ll = grp + BLR_NWARP * k;
+      if (ll < cw && a < w) {
+        double s = 0.0;
+        if (trans) {
+          for (int cc = 0; cc <= a; cc++) s += T[cc + a * BLR_NB] * Z[cc + ll * BLR_NB];
+        } else {
+          for (int cc = a; cc < w; cc++) s += T[a + cc * BLR_NB] * Z[cc + ll * BLR_NB];
+        }
+        W[a + ll * BLR_NB] = s;
+      }
+    }
+    __syncthreads();
+    // top rows: Ct -= W
+    for (int e = threadIdx.x; e < w * cw; e += BLR_NT) {
+      int aa = e % w, ll = e / w;
+      double* cp = Ct + aa + (long long)(c0 + ll) * ldt;
+      *cp = ldg(cp) - W[aa + ll * BLR_NB];
+    }
+    // bottom rows: Cb -= Yb W
+    if (Cb.sr == 1) {
+      for (long long e = threadIdx.x; e < (long long)ry * cw; e += BLR_NT) {
+        int rr = (int)(e % ry), ll = (int)(e / ry);
+        double s = 0.0;
+        for (int aa = 0; aa < w; aa++) s += Yb[rr + aa * ldyb] * W[aa + ll * BLR_NB];
+        double* cp = Cb.at(rr, c0 + ll);
+        *cp = ldg(cp) - s;
+      }
+    } else {
+      for (long long e = threadIdx.x; e < (long long)ry * cw; e += BLR_NT) {
+        int ll = (int)(e % cw), rr = (int)(e / cw);
+        double s = 0.0;
+        for (int aa = 0; aa < w; aa++) s += Yb[rr + aa * ldyb] * W[aa + ll * BLR_NB];
+        double* cp = Cb.at(rr, c0 + ll);
+        *cp = ldg(cp) - s;
+      }
+    }
+    __syncthreads();
+  }
+  c.fma += (2.0 * ry * w + 0.5 * w * w) * nc;
+}
+
+// ---------------------------------------------------------------------------
+// C = alpha op(A) op(B) + beta C, all global, column-major.  beta == 0 never
+// reads C.
+// ---------------------------------------------------------------------------
+__device__ void gemm(int m, int n, int k, double alpha, const double* A, long long lda, bool ta,
+                     const double* B, long long ldb, bool tb, double beta, double* C,
+                     long long ldc, Ctx& c) {
+  double* As = c.s.cs;            // 64 x 16, ld 65
+  double* Bs = c.s.cs + 65 * 16;  // 16 x 64, ld 64
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  for (int tm = 0; tm < m; tm += 64) {
+    for (int tn = 0; tn < n; tn += 64) {
+      double acc[4][4];
+#pragma unroll
+      for (int i = 0; i < 4; i++)
+#pragma unroll
+        for (int j = 0; j < 4; j++) acc[i][j] = 0.0;
+      for (int kk = 0; kk < k; kk += 16) {
+        __syncthreads();
+        for (int e = threadIdx.x; e < 1024; e += BLR_NT) {
+          int r, cc;
+          if (!ta) { r = e & 63; cc = e >> 6; } else { cc = e & 15; r = e >> 4; }
+          int gr = tm + r, gk = kk + cc;
+          double v = 0.0;
+          if (gr < m && gk < k) v = ta ? ldg(A + gk + (long long)gr * lda) : ldg(A + gr + (long long)gk * lda);
+          As[r + cc * 65] = v;
+        }
+        for (int e = threadIdx.x; e < 1024; e += BLR_NT) {
+          int cc, nn;
+          if (!tb) { cc = e & 15; nn = e >> 4; } else { nn = e & 63; cc = e >> 6; }
+          int gk = kk + cc, gn = tn + nn;
+          double v = 0.0;
+          if (gn < n && gk < k) v = tb ? ldg(B + gn + (long long)gk * ldb) : ldg(B + gk + (long long)gn * ldb);
+          Bs[cc * 64 + nn] = v;
+        }
+        __syncthreads();
+        const int kmax = min(16, k - kk);
+        for (int cc = 0; cc < kmax; cc++) {
+          double av[4], bv[4];
+#pragma unroll
+          for (int i = 0; i < 4; i++) av[i] = As[ty + 16 * i + cc * 65];
+#pragma unroll
+          for (int j = 0; j < 4; j++) bv[j] = Bs[cc * 64 + tx + 16 * j];
+#pragma unroll
+          for (int i = 0; i < 4; i++)
+#pragma unroll
+            for (int j = 0; j < 4; j++) acc[i][j] += av[i] * bv[j];
+        }
+      }
+#pragma unroll
+      for (int i = 0; i < 4; i++) {
+#pragma unroll
+        for (int j = 0; j < 4; j++) {
+          int gr = tm + ty + 16 * i, gn = tn + tx + 16 * j;
+          if (gr < m && gn < n) {
+            double* cp = C + gr + (long long)gn * ldc;
+            double v = alpha * acc[i][j];
+            if (beta != 0.0) v += beta * ldg(cp);
+            *cp = v;
+          }
+        }
+      }
+    }
+  }
+  __syncthreads();
+  c.fma += (double)m * n * k;
+}
+
+// ---------------------------------------------------------------------------
+// Blocked Householder QR of a global m x n matrix (m >= n) in place; T
+// blocks (one NB x NB per panel) at Tp + c0*NB (ld NB).
+// ---------------------------------------------------------------------------
+__device__ void geqrf(double* A, long long lda, int m, int n, double* Tp, Ctx& c) {
+  for (int c0 = 0; c0 < n; c0 += BLR_NB) {
+    const int w = min(BLR_NB, n - c0), h = m - c0;
+    if (h <= 0) break;
+    const int ldp = h | 1;
+    __syncthreads();
+    stage_in(c.s.pnl, ldp, colmajor(A + c0 + (long long)c0 * lda, (int)lda), h, w);
+    panel_qr(c.s.pnl, ldp, h, w, c.s.tau, c);
+    gram_panel(c.s.pnl, ldp, h, w, c.s.z, c);
+    t_recur(c.s.z, c.s.tau, w, c.s.t, c);
+    for (int e = threadIdx.x; e < BLR_NB * BLR_NB; e += BLR_NT) {
+      int a = e % BLR_NB, l = e / BLR_NB;
+      if (l < w) Tp[a + (long long)(c0 + l) * BLR_NB] = c.s.t[e];
+    }
+    stage_out(colmajor(A + c0 + (long long)c0 * lda, (int)lda), c.s.pnl, ldp, h, w);
+    if (c0 + w < n)
+      apply_refl_panel(A + c0 + (long long)(c0 + w) * lda, lda, h, n - c0 - w, c.s.pnl, ldp, w,
+                       c.s.t, true, c);
+    __syncthreads();
+  }
+}
+
+// C (m x nc) <- Q^T C (trans) or Q C for Q from geqrf of an m x nref matrix.
+__device__ void apply_q(const double* Y, long long ldy, int m, int nref, const double* Tp, double* C,
+                        long long ldc, int nc, bool trans, Ctx& c) {
+  const int npan = (nref + BLR_NB - 1) / BLR_NB;
+  for (int pi = 0; pi < npan; pi++) {
+    const int pp = trans ? pi : npan - 1 - pi;
+    const int c0 = pp * BLR_NB, w = min(BLR_NB, nref - c0), h = m - c0;
+    if (h <= 0) continue;
+    const int ldp = h | 1;
+    __syncthreads();
+    stage_in(c.s.pnl, ldp, colmajor(const_cast<double*>(Y) + c0 + (long long)c0 * ldy, (int)ldy), h, w);
+    for (int e = threadIdx.x; e < BLR_NB * BLR_NB; e += BLR_NT) {
+      int l = e / BLR_NB;
+      c.s.t[e] = (l < w) ? ldg(Tp + e + (long long)c0 * BLR_NB) : 0.0;
+    }
+    __syncthreads();
+    apply_refl_panel(C + c0, ldc, h, nc, c.s.pnl, ldp, w, c.s.t, trans, c);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Column-pivoted Householder QR of a CTA-private m x n matrix (plain loads),
+// stopped at the smallest r whose trailing block has squared Frobenius norm
+// <= tol2, or when r reaches maxr (then *over = 1 if the tail is still
+// above tol2).  perm (length n, global or shared) receives the column order;
+// tau the reflector scalars.  Column norms are recomputed exactly each step.
+// ---------------------------------------------------------------------------
+__device__ int qrcp(double* A, long long lda, int m, int n, double tol2, int maxr, int* perm,
+                    double* tau, int* over, Ctx& c) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  double* cn = c.s.vec;   // column norms (n <= 512)
+  for (int j = threadIdx.x; j < n; j += BLR_NT) perm[j] = j;
+  if (threadIdx.x == 0) *over = 0;
+  __syncthreads();
+  int r = 0;
+  const int kmax = min(m, n);
+  while (true) {
+    // exact trailing column norms
+    for (int col = r + warp; col < n; col += BLR_NWARP) {
+      double acc = 0.0;
+      const double* ap = A + (long long)col * lda;
+      for (int i = r + lane; i < m; i += 32) acc += ap[i] * ap[i];
+      acc = warp_sum(acc);
+      if (lane == 0) cn[col] = acc;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double tail = 0.0;
+      int piv = r;
+      double best = -1.0;
+      for (int col = r; col < n; col++) {
+        tail += cn[col];
+        if (cn[col] > best) { best = cn[col]; piv = col; }
+      }
+      int stop = 0;
+      if (r >= kmax || tail <= tol2) stop = 1;
+      else if (r == maxr) { stop = 1; *over = 1; }
+      c.s.flag[0] = stop;
+      c.s.flag[1] = piv;
+    }
+    __syncthreads();
+    if (c.s.flag[0]) break;
+    const int piv = c.s.flag[1];
+    c.fma += (double)(m - r) * (n - r);
+    if (piv != r) {
+      for (int i = threadIdx.x; i < m; i += BLR_NT) {
+        double t0 = A[i + (long long)r * lda];
+        A[i + (long long)r * lda] = A[i + (long long)piv * lda];
+        A[i + (long long)piv * lda] = t0;
+      }
+      if (threadIdx.x == 0) {
+        int t0 = perm[r]; perm[r] = perm[piv]; perm[piv] = t0;
+      }
+    }
+    __syncthreads();
+    double* ar = A + (long long)r * lda;
+    double part = 0.0;
+    for (int i = r + 1 + threadIdx.x; i < m; i += BLR_NT) part += ar[i] * ar[i];
+    double sig2 = block_sum(part, c.s.red);
+    if (threadIdx.x == 0) {
+      double beta, tj, sc;
+      house(ar[r], sig2, beta, tj, sc);
+      flag_numeric(c, beta);
+      c.s.scal[0] = beta; c.s.scal[1] = tj; c.s.scal[2] = sc;
+    }
+    __syncthreads();
+    const double tj = c.s.scal[1], sc = c.s.scal[2];
+    for (int i = r + 1 + threadIdx.x; i < m; i += BLR_NT) ar[i] *= sc;
+    __syncthreads();
+    for (int col = r + 1 + warp; col < n; col += BLR_NWARP) {
+      double* ap = A + (long long)col * lda;
+      double acc = 0.0;
+      for (int i = r + 1 + lane; i < m; i += 32) acc += ar[i] * ap[i];
+      acc = warp_sum(acc);
+      double wl = (__shfl_sync(FULLMASK, ap[r], 0) + acc) * tj;
+      if (lane == 0) ap[r] -= wl;
+      for (int i = r + 1 + lane; i < m; i += 32) ap[i] -= wl * ar[i];
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) { ar[r] = c.s.scal[0]; tau[r] = tj; }
+    __syncthreads();
+    c.fma += 2.0 * (m - r) * (n - r);
+    r++;
+  }
+  __syncthreads();
+  return r;
+}
+
+// C (m x nc, CTA-private) <- Q C (trans = false) or Q^T C for the first nr
+// unblocked reflectors stored below the diagonal of A (from qrcp).
+__device__ void apply_q_unblocked(const double* A, long long lda, int m, int nr, const double* tau,
+                                  double* C, long long ldc, int nc, bool trans, Ctx& c) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int jj = 0; jj < nr; jj++) {
+    const int j = trans ? jj : nr - 1 - jj;
+    const double* v = A + (long long)j * lda;
+    const double tj = tau[j];
+    __syncthreads();
+    if (tj != 0.0) {
+      for (int col = warp; col < nc; col += BLR_NWARP) {
+        double* cp = C + (long long)col * ldc;
+        double acc = 0.0;
+        for (int i = j + 1 + lane; i < m; i += 32) acc += v[i] * cp[i];
+        acc = warp_sum(acc);
+        double wl = (__shfl_sync(FULLMASK, cp[j], 0) + acc) * tj;
+        if (lane == 0) cp[j] -= wl;
+        for (int i = j + 1 + lane; i < m; i += 32) cp[i] -= wl * v[i];
+      }
+    }
+  }
+  __syncthreads();
+  c.fma += 2.0 * m * nr * nc;
+}
+
+// ---------------------------------------------------------------------------
+// One-sided (Hestenes) Jacobi on the columns of X (s x s, CTA-private, ld):
+// on exit the columns are mutually orthogonal, X = M V.  sig[j] = ||x_j||
+// and order[0..s) lists the columns by decreasing norm (ties: lower index).
+// Rotations are skipped once |x_p.x_q| <= tol sqrt(|x_p|^2 |x_q|^2).
+// ---------------------------------------------------------------------------
+__device__ void jacobi_svd(double* X, int ldx, int s, double* sig, int* order, Ctx& c) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const double tol = 1e-15;
+  double* nrm = sig;   // squared norms during the sweeps
+  const int np = (s + 1) & ~1;      // padded even count (index s is a dummy)
+  int* pos = order;                 // tournament positions (np <= 512)
+  for (int j = threadIdx.x; j < s; j += BLR_NT) {
+    double acc = 0.0;
+    for (int i = 0; i < s; i++) acc += X[i + j * ldx] * X[i + j * ldx];
+    nrm[j] = acc;
+  }
+  for (int j = threadIdx.x; j < np; j += BLR_NT) pos[j] = j;
+  __syncthreads();
+  int sweeps = 0;
+  for (; sweeps < 40 && s > 1; sweeps++) {
+    if (threadIdx.x == 0) c.s.flag[2] = 0;
+    __syncthreads();
+    for (int round = 0; round < np - 1; round++) {
+      for (int pr = warp; pr < np / 2; pr += BLR_NWARP) {
+        int p = pos[pr], q = pos[np - 1 - pr];
+        if (p >= s || q >= s) continue;
+        if (p > q) { int t0 = p; p = q; q = t0; }
+        double* xp = X + p * ldx;
+        double* xq = X + q * ldx;
+        double g = 0.0;
+        for (int i = lane; i < s; i += 32) g += xp[i] * xq[i];
+        g = warp_sum(g);
+        const double al = nrm[p], be = nrm[q];
+        if (fabs(g) > tol * sqrt(al * be) && g != 0.0) {
+          const double zeta = (be - al) / (2.0 * g);
+          const double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+          const double cs = 1.0 / sqrt(1.0 + t * t), sn = cs * t;
+          for (int i = lane; i < s; i += 32) {
+            double u = xp[i], v = xq[i];
+            xp[i] = cs * u - sn * v;
+            xq[i] = sn * u + cs * v;
+          }
+          __syncwarp();
+          if (lane == 0) {
+            nrm[p] = al - t * g;
+            nrm[q] = be + t * g;
+            c.s.flag[2] = 1;
+          }
+        }
+      }
+      __syncthreads();
+      // rotate tournament positions 1..np-1
+      if (threadIdx.x == 0) {
+        int last = pos[np - 1];
+        for (int i = np - 1; i > 1; i--) pos[i] = pos[i - 1];
+        pos[1] = last;
+      }
+      __syncthreads();
+    }
+    c.fma += 2.5 * (double)s * s * s;
+    // refresh the squared norms exactly
+    for (int j = threadIdx.x; j < s; j += BLR_NT) {
+      double acc = 0.0;
+      for (int i = 0; i < s; i++) acc += X[i + j * ldx] * X[i + j * ldx];
+      nrm[j] = acc;
+    }
+    __syncthreads();
+    if (c.s.flag[2] == 0) break;
+    __syncthreads();
+  }
+  // singular values and descending order
+  for (int j = threadIdx.x; j < s; j += BLR_NT) sig[j] = sqrt(nrm[j]);
+  __syncthreads();
+  for (int j = threadIdx.x; j < s; j += BLR_NT) {
+    int rk = 0;
+    for (int i = 0; i < s; i++) rk += (sig[i] > sig[j]) || (sig[i] == sig[j] && i < j);
+    order[rk] = j;
+  }
+  __syncthreads();
+}
+
+// Smallest r with sum_{l>=r} sig_l^2 <= eps^2 sum sig_l^2 (sig in the given
+// descending order).  Thread 0 computes; all threads return it.
+__device__ int trunc_rank(const double* sig, const int* order, int s, double eps, Ctx& c) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double tot = 0.0;
+    for (int l = 0; l < s; l++) tot += sig[order[l]] * sig[order[l]];
+    int r = s;
+    if (tot == 0.0) r = 0;
+    else {
+      const double thr = (eps * sqrt(tot)) * (eps * sqrt(tot));
+      double tail = 0.0;
+      r = s;
+      for (int l = s - 1; l >= 0; l--) {   // tail[l] = sum_{>= l}
+        double nt = tail + sig[order[l]] * sig[order[l]];
+        if (nt <= thr) { tail = nt; r = l; } else break;
+      }
+    }
+    c.s.flag[3] = r;
+  }
+  __syncthreads();
+  return c.s.flag[3];
+}
+
+// Stage panel c0 of a reduced reflector: Yr(:, c0:c0+w) into c.s.pnl and
+// its T block into c.s.t.  Returns the shared-memory leading dimension.
+__device__ int stage_reflector_panel(View Yr, int ry, int c0, int w, const double* Tik, Ctx& c) {
+  const int ldy = ry | 1;
+  __syncthreads();
+  View src{Yr.p + c0 * Yr.sc, Yr.sr, Yr.sc};
+  stage_in(c.s.pnl, ldy, src, ry, w);
+  for (int e = threadIdx.x; e < BLR_NB * BLR_NB; e += BLR_NT) {
+    int l = e / BLR_NB;
+    c.s.t[e] = (l < w) ? ldg(Tik + e + (size_t)c0 * BLR_NB) : 0.0;
+  }
+  __syncthreads();
+  return ldy;
+}
+
+// [Ctop (b x nc, ld ldt); Cbot (ry x nc)] <- Q^T (trans) or Q times it, for
+// the reduced reflector Q = I - [I; Yr] T [I; Yr]^T of a TSQRT (b reflectors
+// in blocks of 32).
+__device__ void apply_ts_reflector(View Yr, int ry, int b, const double* Tik, double* Ctop,
+                                   long long ldt, View Cbot, int nc, bool trans, Ctx& c) {
+  const int npan = b / BLR_NB;
+  for (int pi = 0; pi < npan; pi++) {
+    const int pp = trans ? pi : npan - 1 - pi;
+    const int c0 = pp * BLR_NB;
+    const int ldy = stage_reflector_panel(Yr, ry, c0, BLR_NB, Tik, c);
+    apply_refl_ts(Ctop + c0, ldt, Cbot, ry, nc, c.s.pnl, ldy, BLR_NB, c.s.t, trans, c);
+  }
+}
+
+}  // namespace

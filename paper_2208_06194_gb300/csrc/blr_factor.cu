@@ -1,0 +1,721 @@
+// Tiled Householder BLR-QR (Algorithm 4 with the BLR tile kernels of
+// Section 3.4) as one persistent device-side task scheduler (Section 4.3).
+//
+// Storage: tile (i,j) owns b*b doubles; a dense tile is b x b column-major;
+// a low-rank tile of rank r keeps U (b x r) at offset 0 and V (b x r) at
+// offset b*(b/2).  After the factorization tile (i,k), i > k, holds
+// Y~_ik = U_ik Y_ik with Y_ik^T in the V slot (Section 3.4.3), or a dense
+// Y_ik.  Every reflector block is kept in compact-WY form with inner
+// blocking: the T of each 32 consecutive reflectors (Eq. 3, Eq. 21).
+#include <cstdio>
+#include <cstdlib>
+#include <algorithm>
+#include <vector>
+#include "blr_device.cuh"
+#include "blr_dag.h"
+
+namespace {
+
+// Bump allocator over the CTA's private scratch slab.  The slab holds
+// BLR_SLAB_B2 * b^2 doubles, more than any task needs, and no single request
+// exceeds 2 b^2; should the total ever run over, the request is served from
+// the slab's start (still in bounds) and the overflow flag fails the call.
+struct TaskEnv {
+  const SchedParams* P;
+  double* slab;
+  size_t used;
+  bool overflow;
+  __device__ double* alloc(size_t n) {
+    const size_t nn = (n + 31) & ~(size_t)31;   // 256-byte granules
+    if (used + nn > P->slab) {
+      overflow = true;
+      return slab;
+    }
+    double* p = slab + used;
+    used += nn;
+    return p;
+  }
+};
+
+__device__ __forceinline__ double* tile_ptr(const SchedParams& P, int i, int j) {
+  return P.tiles + ((size_t)j * P.p + i) * (size_t)P.b * P.b;
+}
+__device__ __forceinline__ int* rank_ptr(const SchedParams& P, int i, int j) {
+  return P.rank + (size_t)j * P.p + i;
+}
+__device__ __forceinline__ double* t_ptr(const SchedParams& P, int i, int k) {
+  return P.t + (size_t)(P.toff_dev[k] + (i - k)) * BLR_NB * P.b;
+}
+__device__ __forceinline__ int ld_rank(const int* p) { return __ldcg(p); }
+
+// ---------------------------------------------------------------------------
+// TSQRT panel: Householder on [Rp (w x w upper, ld NB); Bp (ry x w, ld ldb)],
+// reflector j = [e_j; y_j] (Section 3.4.3).
+// ---------------------------------------------------------------------------
+__device__ void ts_panel_qr(double* Rp, double* Bp, int ldb, int ry, int w, double* tau, Ctx& c) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  __syncthreads();
+  for (int j = 0; j < w; j++) {
+    double part = 0.0;
+    for (int s = threadIdx.x; s < ry; s += BLR_NT) {
+      double x = Bp[s + j * ldb];
+      part += x * x;
+    }
+    double sig2 = block_sum(part, c.s.red);
+    if (threadIdx.x == 0) {
+      double beta, tj, sc;
+      house(Rp[j + j * BLR_NB], sig2, beta, tj, sc);
+      flag_numeric(c, beta);
+      c.s.scal[0] = beta;
+      c.s.scal[1] = tj;
+      c.s.scal[2] = sc;
+    }
+    __syncthreads();
+    const double tj = c.s.scal[1], sc = c.s.scal[2];
+    for (int s = threadIdx.x; s < ry; s += BLR_NT) Bp[s + j * ldb] *= sc;
+    __syncthreads();
+    for (int l = j + 1 + warp; l < w; l += BLR_NWARP) {
+      double acc = 0.0;
+      for (int s = lane; s < ry; s += 32) acc += Bp[s + j * ldb] * Bp[s + l * ldb];
+      acc = warp_sum(acc);
+      double wl = (__shfl_sync(FULLMASK, Rp[j + l * BLR_NB], 0) + acc) * tj;
+      if (lane == 0) Rp[j + l * BLR_NB] -= wl;
+      for (int s = lane; s < ry; s += 32) Bp[s + l * ldb] -= wl * Bp[s + j * ldb];
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      Rp[j + j * BLR_NB] = c.s.scal[0];
+      tau[j] = tj;
+    }
+    __syncthreads();
+  }
+  c.fma += (double)ry * w * w;
+}
+
+// ---------------------------------------------------------------------------
+// Rounded addition (Algorithm 6) for C = Uf H0^T where H has already been
+// QR-factored in place (R_H in its top s x s, reflectors below, T blocks TH):
+// QR(Uf), M = R_U R_H^T, SVD(M) by one-sided Jacobi, keep the first r_eps
+// columns: U_C = Q_U u_r, V_C = Q_H (M^T u_r).  Uf is overwritten.  A result
+// with rank > dense_rank is written as the dense product Uf0 H0^T.
+// ---------------------------------------------------------------------------
+__device__ void recompress_side(TaskEnv& env, double* Uf, int ldu, const double* H, const double* TH,
+                                const double* H0, int s, double* dest, int* dest_rank, Ctx& c) {
+  const SchedParams& P = *env.P;
+  const int b = P.b;
+  const size_t mark = env.used;
+  if (s == 0) {
+    if (threadIdx.x == 0) *dest_rank = 0;
+    __syncthreads();
+    return;
+  }
+  double* U0 = env.alloc((size_t)b * s);
+  copy_mat(U0, b, Uf, ldu, b, s);
+  double* TU = env.alloc((size_t)BLR_NB * s);
+  __syncthreads();
+  geqrf(Uf, ldu, b, s, TU, c);
+  // M = R_U R_H^T  (upper triangular factors)
+  double* RU = env.alloc((size_t)s * s);
+  double* RH = env.alloc((size_t)s * s);
+  for (int e = threadIdx.x; e < s * s; e += BLR_NT) {
+    int a = e % s, l = e / s;
+    RU[e] = (a <= l) ? ldg(Uf + a + (size_t)l * ldu) : 0.0;
+    RH[e] = (a <= l) ? ldg(H + a + (size_t)l * b) : 0.0;
+  }
+  __syncthreads();
+  double* M0 = env.alloc((size_t)s * s);
+  gemm(s, s, s, 1.0, RU, s, false, RH, s, true, 0.0, M0, s, c);
+  // Jacobi on a copy of M (shared memory when it fits)
+  double* X;
+  int ldx;
+  if (s <= 126) {
+    X = c.s.pnl;
+    ldx = s | 1;
+  } else {
+    X = env.alloc((size_t)s * s);
+    ldx = s;
+  }
+  for (int e = threadIdx.x; e < s * s; e += BLR_NT) {
+    int a = e % s, l = e / s;
+    X[a + l * ldx] = M0[e];
+  }
+  __syncthreads();
+  double* sig = c.s.vec;
+  int* order = c.s.ivec;
+  jacobi_svd(X, ldx, s, sig, order, c);
+  const int r = trunc_rank(sig, order, s, P.rec_tol, c);
+  if (r > P.dense_rank) {
+    // dense fallback: the exact sum
+    gemm(b, b, s, 1.0, U0, b, false, H0, b, true, 0.0, dest, b, c);
+    __syncthreads();
+    if (threadIdx.x == 0) *dest_rank = -1;
+    __syncthreads();
+    env.used = mark;
+    return;
+  }
+  // u_r (s x r) and v_r sigma_r = M^T u_r
+  double* Ub = env.alloc((size_t)s * (r > 0 ? r : 1));
+  for (int e = threadIdx.x; e < s * r; e += BLR_NT) {
+    int a = e % s, l = e / s;
+    int col = order[l];
+    Ub[e] = X[a + col * ldx] / sig[col];
+  }
+  __syncthreads();
+  double* CU = env.alloc((size_t)b * (r > 0 ? r : 1));
+  double* CV = env.alloc((size_t)b * (r > 0 ? r : 1));
+  if (r > 0) {
+    zero_mat(CU, b, b, r);
+    zero_mat(CV, b, b, r);
+    __syncthreads();
+    copy_mat(CU, b, Ub, s, s, r);
+    gemm(s, r, s, 1.0, M0, s, true, Ub, s, false, 0.0, CV, b, c);
+    apply_q(Uf, ldu, b, s, TU, CU, b, r, false, c);
+    apply_q(H, b, b, s, TH, CV, b, r, false, c);
+    copy_mat(dest, b, CU, b, b, r);
+    copy_mat(dest + (size_t)b * P.cap, b, CV, b, b, r);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) *dest_rank = r;
+  __syncthreads();
+  env.used = mark;
+}
+
+// ---------------------------------------------------------------------------
+// Task bodies
+// ---------------------------------------------------------------------------
+
+// GEQRT(k): Householder QR of the dense diagonal tile (Section 3.4.1).
+__device__ void task_geqrt(TaskEnv& env, int k, Ctx& c) {
+  const SchedParams& P = *env.P;
+  double* A = tile_ptr(P, k, k);
+  geqrf(A, P.b, P.b, P.b, t_ptr(P, k, k), c);
+}
+
+// LARFB(k,j): R_kj = Q_kk^T A_kj (Section 3.4.2): U <- Q^T U, or the dense tile.
+__device__ void task_larfb(TaskEnv& env, int k, int j, Ctx& c) {
+  const SchedParams& P = *env.P;
+  const int b = P.b;
+  const int r = ld_rank(rank_ptr(P, k, j));
+  double* C = tile_ptr(P, k, j);
+  const int nc = (r < 0) ? b : r;
+  if (nc > 0) apply_q(tile_ptr(P, k, k), b, b, b, t_ptr(P, k, k), C, b, nc, true, c);
+}
+
+// TSQRT(i,k): QR([R_kk; A^V_ik]) with A^V = V^T (low-rank) or the dense tile
+// (Section 3.4.3, Eqs. 19-21); Y_ik overwrites A^V in place.
+__device__ void task_tsqrt(TaskEnv& env, int i, int k, Ctx& c) {
+  const SchedParams& P = *env.P;
+  const int b = P.b;
+  const int r = ld_rank(rank_ptr(P, i, k));
+  double* R = tile_ptr(P, k, k);
+  double* Tk = t_ptr(P, i, k);
+  double* B = tile_ptr(P, i, k);
+  const int ry = (r < 0) ? b : r;
+  View Bv = (r < 0) ? colmajor(B, b) : rowmajor(B + (size_t)b * P.cap, b);
+  if (ry == 0) {
+    for (int e = threadIdx.x; e < BLR_NB * b; e += BLR_NT) Tk[e] = 0.0;
+    __syncthreads();
+    return;
+  }
+  for (int c0 = 0; c0 < b; c0 += BLR_NB) {
+    const int w = BLR_NB;
+    const int ldb = ry | 1;
+    __syncthreads();
+    for (int e = threadIdx.x; e < w * w; e += BLR_NT) {
+      int a = e % w, l = e / w;
+      c.s.rp[a + l * BLR_NB] = (a <= l) ? ldg(R + (c0 + a) + (size_t)(c0 + l) * b) : 0.0;
+    }
+    View Bp{Bv.p + c0 * Bv.sc, Bv.sr, Bv.sc};
+    stage_in(c.s.pnl, ldb, Bp, ry, w);
+    ts_panel_qr(c.s.rp, c.s.pnl, ldb, ry, w, c.s.tau, c);
+    gram_dense(c.s.pnl, ldb, ry, w, c.s.z, c);
+    t_recur(c.s.z, c.s.tau, w, c.s.t, c);
+    for (int e = threadIdx.x; e < BLR_NB * BLR_NB; e += BLR_NT) Tk[e + (size_t)c0 * BLR_NB] = c.s.t[e];
+    for (int e = threadIdx.x; e < w * w; e += BLR_NT) {
+      int a = e % w, l = e / w;
+      if (a <= l) R[(c0 + a) + (size_t)(c0 + l) * b] = c.s.rp[a + l * BLR_NB];
+    }
+    stage_out(Bp, c.s.pnl, ldb, ry, w);
+    if (c0 + w < b) {
+      View Cb{Bv.p + (c0 + w) * Bv.sc, Bv.sr, Bv.sc};
+      apply_refl_ts(R + c0 + (size_t)(c0 + w) * b, b, Cb, ry, b - c0 - w, c.s.pnl, ldb, w, c.s.t,
+                    true, c);
+    }
+    __syncthreads();
+  }
+}
+
+// TPMQRT(i,j,k): [R_kj; A_ij] <- Q_ik^T [R_kj; A_ij] with
+// Q_ik = I - [I; Y~] T [I; Y~]^T (Section 3.4.4).  With Y~ = U_ik Y_ik the
+// operator acts on A_ij only through P = U_ik^T A_ij, so it is applied to
+// the reduced pair [R_kj; P] (rows b + r_Y) and A_ij += U_ik (P' - P).  When
+// R_kj and A_ij are low-rank the pair is kept factored, [R; P] = G H^T, the
+// reflector is applied to G, and both results are recompressed by the
+// rounded addition of Algorithm 6 (sharing the QR of H).
+__device__ void task_tpmqrt(TaskEnv& env, int i, int j, int k, Ctx& c) {
+  const SchedParams& P = *env.P;
+  const int b = P.b, cap = P.cap;
+  const int rY = ld_rank(rank_ptr(P, i, k));
+  const int rR = ld_rank(rank_ptr(P, k, j));
+  const int rA = ld_rank(rank_ptr(P, i, j));
+  const bool ylr = rY >= 0;
+  if (ylr && rY == 0) return;           // the reflector is the identity
+  const int ry = ylr ? rY : b;
+  double* Yt = tile_ptr(P, i, k);
+  double* Uy = Yt;                      // U_ik when low-rank
+  View Yr = ylr ? rowmajor(Yt + (size_t)b * cap, b) : colmajor(Yt, b);
+  const double* Tik = t_ptr(P, i, k);
+  double* Rt = tile_ptr(P, k, j);
+  double* At = tile_ptr(P, i, j);
+  int* rankR = rank_ptr(P, k, j);
+  int* rankA = rank_ptr(P, i, j);
+
+  if (rR >= 0 && (rA >= 0 || ylr)) {
+    // ---------------- factored paths -----------------
+    const bool adense = rA < 0;         // F2: A dense, Y low-rank
+    const int s2 = adense ? ry : rA;    // columns of the P part
+    const int s = rR + s2;
+    if (s == 0) return;
+    const int ldG = b + ry;
+    double* G = env.alloc((size_t)ldG * s);
+    double* H = env.alloc((size_t)b * s);
+    double* H0 = env.alloc((size_t)b * s);
+    double* PU0 = env.alloc((size_t)ry * s2);
+    zero_mat(G, ldG, ldG, s);
+    __syncthreads();
+    copy_mat(G, ldG, Rt, b, b, rR);                              // U_R
+    copy_mat(H, b, Rt + (size_t)b * cap, b, b, rR);              // V_R
+    if (!adense) {
+      // P = (U_ik^T U_A) V_A^T: G_bot(:, rR:) = U_ik^T U_A, H(:, rR:) = V_A
+      if (ylr) gemm(ry, rA, b, 1.0, Uy, b, true, At, b, false, 0.0, G + b + (size_t)rR * ldG, ldG, c);
+      else copy_mat(G + b + (size_t)rR * ldG, ldG, At, b, b, rA);
+      copy_mat(H + (size_t)rR * b, b, At + (size_t)b * cap, b, b, rA);
+    } else {
+      // P = U_ik^T A (ry x b): G_bot(:, rR:) = I, H(:, rR:) = P^T
+      gemm(b, ry, b, 1.0, At, b, true, Uy, b, false, 0.0, H + (size_t)rR * b, b, c);
+      __syncthreads();
+      for (int e = threadIdx.x; e < ry; e += BLR_NT) G[b + e + (size_t)(rR + e) * ldG] = 1.0;
+    }
+    __syncthreads();
+    copy_mat(PU0, ry, G + b + (size_t)rR * ldG, ldG, ry, s2);
+    copy_mat(H0, b, H, b, b, s);
+    __syncthreads();
+    // apply the reduced reflector to G
+    apply_ts_reflector(Yr, ry, b, Tik, G, ldG, colmajor(G + b, ldG), s, true, c);
+    // Delta G = G_bot' - G_bot
+    for (int e = threadIdx.x; e < ry * s2; e += BLR_NT) {
+      int a = e % ry, l = e / ry;
+      G[b + a + (size_t)(rR + l) * ldG] -= PU0[e];
+    }
+    __syncthreads();
+    if (!adense) {
+      // A_new = Uf_A H^T with Uf_A = U_ik dG + [0, U_A] (or dG + [0, U_A] for dense Y)
+      double* UfA = env.alloc((size_t)b * s);
+      if (ylr) gemm(b, s, ry, 1.0, Uy, b, false, G + b, ldG, false, 0.0, UfA, b, c);
+      else copy_mat(UfA, b, G + b, ldG, b, s);
+      __syncthreads();
+      for (int e = threadIdx.x; e < b * rA; e += BLR_NT) {
+        int a = e % b, l = e / b;
+        UfA[a + (size_t)(rR + l) * b] += ldg(At + a + (size_t)l * b);
+      }
+      __syncthreads();
+      double* TH = env.alloc((size_t)BLR_NB * s);
+      geqrf(H, b, b, s, TH, c);
+      recompress_side(env, G, ldG, H, TH, H0, s, Rt, rankR, c);
+      recompress_side(env, UfA, b, H, TH, H0, s, At, rankA, c);
+    } else {
+      // A += (U_ik dG) H0^T (dense update), then recompress R
+      double* M1 = env.alloc((size_t)b * s);
+      gemm(b, s, ry, 1.0, Uy, b, false, G + b, ldG, false, 0.0, M1, b, c);
+      gemm(b, b, s, 1.0, M1, b, false, H0, b, true, 1.0, At, b, c);
+      double* TH = env.alloc((size_t)BLR_NB * s);
+      geqrf(H, b, b, s, TH, c);
+      recompress_side(env, G, ldG, H, TH, H0, s, Rt, rankR, c);
+    }
+    return;
+  }
+
+  // ---------------- dense path: R_kj dense (or becomes dense) -----------------
+  double* Rd;
+  bool r_scratch = false;
+  if (rR < 0) {
+    Rd = Rt;
+  } else {
+    // R low-rank with dense Y and dense A: R + Y~^T A is dense (OP1)
+    Rd = env.alloc((size_t)b * b);
+    if (rR > 0) gemm(b, b, rR, 1.0, Rt, b, false, Rt + (size_t)b * cap, b, true, 0.0, Rd, b, c);
+    else zero_mat(Rd, b, b, b);
+    r_scratch = true;
+  }
+  double* Pm;
+  int ldp;
+  double* P0 = nullptr;
+  bool a_inplace = false;
+  if (ylr) {
+    ldp = ry;
+    Pm = env.alloc((size_t)ry * b);
+    if (rA < 0) {
+      gemm(ry, b, b, 1.0, Uy, b, true, At, b, false, 0.0, Pm, ry, c);
+    } else if (rA == 0) {
+      zero_mat(Pm, ry, ry, b);
+    } else {
+      double* PU = env.alloc((size_t)ry * rA);
+      gemm(ry, rA, b, 1.0, Uy, b, true, At, b, false, 0.0, PU, ry, c);
+      gemm(ry, b, rA, 1.0, PU, ry, false, At + (size_t)b * cap, b, true, 0.0, Pm, ry, c);
+    }
+    P0 = env.alloc((size_t)ry * b);
+    __syncthreads();
+    copy_mat(P0, ry, Pm, ry, ry, b);
+  } else {
+    ldp = b;
+    if (rA < 0) {
+      Pm = At;
+      a_inplace = true;
+    } else {
+      Pm = env.alloc((size_t)b * b);
+      if (rA > 0) gemm(b, b, rA, 1.0, At, b, false, At + (size_t)b * cap, b, true, 0.0, Pm, b, c);
+      else zero_mat(Pm, b, b, b);
+    }
+  }
+  __syncthreads();
+  apply_ts_reflector(Yr, ry, b, Tik, Rd, b, colmajor(Pm, ldp), b, true, c);
+  if (r_scratch) {
+    copy_mat(Rt, b, Rd, b, b, b);
+    __syncthreads();
+    if (threadIdx.x == 0) *rankR = -1;
+  }
+  __syncthreads();
+  if (!ylr) {
+    if (!a_inplace) {
+      copy_mat(At, b, Pm, b, b, b);
+      __syncthreads();
+      if (threadIdx.x == 0) *rankA = -1;
+    }
+    __syncthreads();
+    return;
+  }
+  // dP = P' - P
+  for (int e = threadIdx.x; e < ry * b; e += BLR_NT) Pm[e] -= P0[e];
+  __syncthreads();
+  if (rA < 0) {
+    gemm(b, b, ry, 1.0, Uy, b, false, Pm, ry, false, 1.0, At, b, c);
+    return;
+  }
+  // A_new = [U_A, U_ik] [V_A, dP^T]^T, recompressed
+  const int s = rA + ry;
+  double* Uf = env.alloc((size_t)b * s);
+  double* H = env.alloc((size_t)b * s);
+  double* H0 = env.alloc((size_t)b * s);
+  copy_mat(Uf, b, At, b, b, rA);
+  copy_mat(Uf + (size_t)rA * b, b, Uy, b, b, ry);
+  copy_mat(H, b, At + (size_t)b * cap, b, b, rA);
+  __syncthreads();
+  for (int e = threadIdx.x; e < b * ry; e += BLR_NT) {
+    int a = e % b, l = e / b;      // H(:, rA + l) = dP(l, :)^T
+    H[a + (size_t)(rA + l) * b] = Pm[l + (size_t)a * ldp];
+  }
+  __syncthreads();
+  copy_mat(H0, b, H, b, b, s);
+  double* TH = env.alloc((size_t)BLR_NB * s);
+  __syncthreads();
+  geqrf(H, b, b, s, TH, c);
+  recompress_side(env, Uf, b, H, TH, H0, s, At, rankA, c);
+}
+
+// ---------------------------------------------------------------------------
+// Persistent scheduler
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ unsigned long long gtimer() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ void q_push(const SchedParams& P, int qi, int task) {
+  int pos = atomicAdd(P.qtail + qi * 32, 1);
+  atomicExch(P.qbuf + (size_t)qi * P.n_tasks + pos, task);
+}
+
+// Thread 0 only.  Returns a task id, or -1 when the factorization is done
+// or aborted.  Every wait is bounded by the watchdog budget.
+__device__ int q_pop(const SchedParams& P) {
+  unsigned ns = 64;
+  while (true) {
+    if (*(volatile int*)P.status != 0) return -1;
+    for (int qi = 0; qi < BLR_NQ; qi++) {
+      volatile int* head = P.qhead + qi * 32;
+      volatile int* tail = P.qtail + qi * 32;
+      while (true) {
+        int h = *head, t = *tail;
+        if (h >= t) break;
+        if (atomicCAS((int*)head, h, h + 1) == h) {
+          volatile int* slot = P.qbuf + (size_t)qi * P.n_tasks + h;
+          int v;
+          unsigned long long t0 = gtimer();
+          while ((v = *slot) < 0) {
+            if (gtimer() - t0 > (unsigned long long)P.watchdog_ns) {
+              atomicOr(P.status, ST_TIMEOUT);
+              return -1;
+            }
+            __nanosleep(32);
+          }
+          __threadfence();
+          return v;
+        }
+      }
+    }
+    if (*(volatile int*)P.done >= P.n_tasks) return -1;
+    unsigned long long now = gtimer();
+    unsigned long long last = *(volatile unsigned long long*)P.progress_ns;
+    if (last == 0ull) {
+      atomicCAS(P.progress_ns, 0ull, now);
+    } else if (now > last && now - last > (unsigned long long)P.watchdog_ns) {
+      atomicOr(P.status, ST_TIMEOUT);
+      return -1;
+    }
+    __nanosleep(ns);
+    if (ns < 8192) ns <<= 1;
+  }
+}
+
+__global__ void __launch_bounds__(BLR_NT, 1) k_factor(SchedParams P) {
+  extern __shared__ double smem[];
+  __shared__ int task_sh;
+  Ctx c;
+  c.s = sm_carve(smem);
+  c.status = P.status;
+  DagShape d{P.p, P.q, P.off_larfb, P.off_tsqrt, P.off_tpmqrt};
+  TaskEnv env{&P, P.scratch + (size_t)blockIdx.x * P.slab, 0, false};
+  while (true) {
+    if (threadIdx.x == 0) task_sh = q_pop(P);
+    __syncthreads();
+    const int task = task_sh;
+    __syncthreads();
+    if (task < 0) break;
+    int i, j, k;
+    const int type = dag_decode(d, task, &i, &j, &k);
+    c.fma = 0.0;
+    env.used = 0;
+    env.overflow = false;
+    switch (type) {
+      case TASK_GEQRT: task_geqrt(env, k, c); break;
+      case TASK_LARFB: task_larfb(env, k, j, c); break;
+      case TASK_TSQRT: task_tsqrt(env, i, k, c); break;
+      case TASK_TPMQRT: task_tpmqrt(env, i, j, k, c); break;
+      default:
+        if (threadIdx.x == 0) atomicOr(P.status, ST_BADTASK);
+        break;
+    }
+    if (env.overflow && threadIdx.x == 0) atomicOr(P.status, ST_RANK);
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0 && type >= 0) {
+      dag_for_each_successor(d, type, i, j, k, [&](int sid) {
+        if (atomicSub(P.deps + sid, 1) == 1) {
+          __threadfence();
+          int si, sj, sk;
+          const int st = dag_decode(d, sid, &si, &sj, &sk);
+          q_push(P, dag_queue(st, si, sj, sk), sid);
+        }
+      });
+      atomicAdd(P.flops + type, 2.0 * c.fma);
+      atomicAdd(P.ntask + type, 1ull);
+      atomicExch(P.progress_ns, gtimer());
+      __threadfence();
+      atomicAdd(P.done, 1);
+    }
+  }
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// Host side of blr_qr
+// ---------------------------------------------------------------------------
+int blr_launch_factor(blr_factor* f, const blr_opts* o, cudaStream_t st) {
+  blr_matrix& A = f->a;
+  const int p = A.p, q = A.q, b = A.b;
+  std::vector<int> offL(q + 1), offS(q + 1), offP(q + 1);
+  const int n_tasks = dag_offsets(p, q, offL.data(), offS.data(), offP.data());
+  DagShape d{p, q, offL.data(), offS.data(), offP.data()};
+  std::vector<int> deps(n_tasks);
+  for (int id = 0; id < n_tasks; id++) {
+    int i, j, k;
+    int t = dag_decode(d, id, &i, &j, &k);
+    deps[id] = dag_indegree(t, i, j, k);
+  }
+  std::vector<long long> toff(q);
+  long long acc = 0;
+  for (int k = 0; k < q; k++) { toff[k] = acc; acc += p - k; }
+
+  const int nsm = blr_num_sms();
+  int ctas = o->sched_ctas > 0 ? o->sched_ctas : nsm;
+  const size_t slab = (size_t)BLR_SLAB_B2 * b * b;
+
+  // one device block for all scheduler state
+  size_t bytes = 0;
+  auto take = [&](size_t n) { size_t off = bytes; bytes += (n + 255) & ~(size_t)255; return off; };
+  const size_t o_offL = take(sizeof(int) * (q + 1)), o_offS = take(sizeof(int) * (q + 1)),
+               o_offP = take(sizeof(int) * (q + 1)), o_toff = take(sizeof(long long) * q),
+               o_deps = take(sizeof(int) * n_tasks), o_qbuf = take(sizeof(int) * (size_t)BLR_NQ * n_tasks),
+               o_qh = take(sizeof(int) * 32 * BLR_NQ), o_qt = take(sizeof(int) * 32 * BLR_NQ),
+               o_done = take(sizeof(int)), o_status = take(sizeof(int)),
+               o_prog = take(sizeof(unsigned long long)), o_flops = take(sizeof(double) * 4),
+               o_ntask = take(sizeof(unsigned long long) * 4);
+  char* base = nullptr;
+  double* scratch = nullptr;
+  if (cudaMalloc(&base, bytes) != cudaSuccess) { blr_set_error("blr_qr: out of device memory (scheduler state)"); return BLR_ERR_OOM; }
+  if (cudaMalloc(&scratch, sizeof(double) * slab * ctas) != cudaSuccess) {
+    cudaFree(base);
+    blr_set_error("blr_qr: out of device memory (scratch %zu MB)", sizeof(double) * slab * ctas >> 20);
+    return BLR_ERR_OOM;
+  }
+  int rc = BLR_OK;
+  SchedParams P{};
+  P.p = p; P.q = q; P.b = b; P.cap = A.cap;
+  P.dense_rank = (o->dense_rank > 0 && o->dense_rank <= A.cap) ? o->dense_rank : A.cap;
+  P.precision = o->precision;
+  P.rec_tol = o->rec_tol > 0 ? o->rec_tol : o->tol;
+  P.tiles = A.tiles; P.rank = A.rank; P.t = f->t;
+  P.toff_dev = (const long long*)(base + o_toff);
+  P.off_larfb = (const int*)(base + o_offL);
+  P.off_tsqrt = (const int*)(base + o_offS);
+  P.off_tpmqrt = (const int*)(base + o_offP);
+  P.n_tasks = n_tasks;
+  P.deps = (int*)(base + o_deps);
+  P.qbuf = (int*)(base + o_qbuf);
+  P.qhead = (int*)(base + o_qh);
+  P.qtail = (int*)(base + o_qt);
+  P.done = (int*)(base + o_done);
+  P.status = (int*)(base + o_status);
+  P.progress_ns = (unsigned long long*)(base + o_prog);
+  P.watchdog_ns = (long long)(o->watchdog_ms > 0 ? o->watchdog_ms : 20000) * 1000000ll;
+  P.scratch = scratch;
+  P.slab = slab;
+  P.flops = (double*)(base + o_flops);
+  P.ntask = (unsigned long long*)(base + o_ntask);
+
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  do {
+    if ((rc = blr_cuda_check(cudaMemsetAsync(base, 0, bytes, st), "memset scheduler"))) break;
+    if ((rc = blr_cuda_check(cudaMemsetAsync(P.qbuf, 0xff, sizeof(int) * (size_t)BLR_NQ * n_tasks, st), "memset queues"))) break;
+    if ((rc = blr_cuda_check(cudaMemcpyAsync((void*)P.off_larfb, offL.data(), sizeof(int) * (q + 1), cudaMemcpyHostToDevice, st), "copy offsets"))) break;
+    if ((rc = blr_cuda_check(cudaMemcpyAsync((void*)P.off_tsqrt, offS.data(), sizeof(int) * (q + 1), cudaMemcpyHostToDevice, st), "copy offsets"))) break;
+    if ((rc = blr_cuda_check(cudaMemcpyAsync((void*)P.off_tpmqrt, offP.data(), sizeof(int) * (q + 1), cudaMemcpyHostToDevice, st), "copy offsets"))) break;
+    if ((rc = blr_cuda_check(cudaMemcpyAsync((void*)P.toff_dev, toff.data(), sizeof(long long) * q, cudaMemcpyHostToDevice, st), "copy T offsets"))) break;
+    if ((rc = blr_cuda_check(cudaMemcpyAsync(P.deps, deps.data(), sizeof(int) * n_tasks, cudaMemcpyHostToDevice, st), "copy deps"))) break;
+    // the only initially ready task: GEQRT(0) in queue 0
+    int first = 0, one = 1;
+    if ((rc = blr_cuda_check(cudaMemcpyAsync(P.qbuf, &first, sizeof(int), cudaMemcpyHostToDevice, st), "seed queue"))) break;
+    if ((rc = blr_cuda_check(cudaMemcpyAsync(P.qtail, &one, sizeof(int), cudaMemcpyHostToDevice, st), "seed queue"))) break;
+    if ((rc = blr_cuda_check(cudaFuncSetAttribute(k_factor, cudaFuncAttributeMaxDynamicSharedMemorySize, BLR_SMEM_BYTES), "smem attribute"))) break;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    cudaEventRecord(e0, st);
+    k_factor<<<ctas, BLR_NT, BLR_SMEM_BYTES, st>>>(P);
+    if ((rc = blr_cuda_check(cudaGetLastError(), "launch k_factor"))) break;
+    cudaEventRecord(e1, st);
+    if ((rc = blr_cuda_check(cudaStreamSynchronize(st), "k_factor"))) break;
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    f->seconds = ms * 1e-3;
+    int status = 0, done = 0;
+    double fl[4];
+    unsigned long long nt[4];
+    cudaMemcpy(&status, P.status, sizeof(int), cudaMemcpyDeviceToHost);
+    cudaMemcpy(&done, P.done, sizeof(int), cudaMemcpyDeviceToHost);
+    cudaMemcpy(fl, P.flops, sizeof(fl), cudaMemcpyDeviceToHost);
+    cudaMemcpy(nt, P.ntask, sizeof(nt), cudaMemcpyDeviceToHost);
+    f->flops[4] = 0;
+    for (int t = 0; t < 4; t++) { f->flops[t] = fl[t]; f->flops[4] += fl[t]; f->tasks[t] = (long long)nt[t]; }
+    if (status & ST_TIMEOUT) { blr_set_error("blr_qr: scheduler watchdog expired (%d of %d tasks done)", done, n_tasks); rc = BLR_ERR_TIMEOUT; break; }
+    if (status & ST_NUMERIC) { blr_set_error("blr_qr: non-finite Householder coefficient"); rc = BLR_ERR_NUMERIC; break; }
+    if (status & ST_RANK) { blr_set_error("blr_qr: scratch slab exceeded"); rc = BLR_ERR_RANK_OVERFLOW; break; }
+    if (status != 0 || done != n_tasks) { blr_set_error("blr_qr: scheduler ended with status %d, %d of %d tasks", status, done, n_tasks); rc = BLR_ERR_CUDA; break; }
+  } while (0);
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  cudaFree(scratch);
+  cudaFree(base);
+  return rc;
+}
+
+// Host-side check of the DAG formulas (no device work): builds the DAG from
+// dag_successors, checks every in-degree against dag_indegree, and runs the
+// counter protocol in a seeded random order, checking that each task runs
+// exactly once, after all of its predecessors, and that the per-tile writer
+// chains of Algorithm 4 are respected.  Returns 0 on success, or a positive
+// code naming the first failed check.
+extern "C" int blr_dag_selfcheck(int p, int q, unsigned seed) {
+  if (p < 1 || q < 1 || q > p) return 100;
+  std::vector<int> offL(q + 1), offS(q + 1), offP(q + 1);
+  const int n = dag_offsets(p, q, offL.data(), offS.data(), offP.data());
+  DagShape d{p, q, offL.data(), offS.data(), offP.data()};
+  std::vector<int> indeg(n, 0), deps(n), order_done(n, -1);
+  int bad = 0;
+  for (int id = 0; id < n; id++) {
+    int i, j, k;
+    int t = dag_decode(d, id, &i, &j, &k);
+    if (t < 0) return 1;
+    if (t == 0 && dag_id_geqrt(d, k) != id) return 11;
+    if (t == 1 && dag_id_larfb(d, k, j) != id) return 11;
+    if (t == 2 && dag_id_tsqrt(d, i, k) != id) return 11;
+    if (t == 3 && dag_id_tpmqrt(d, i, j, k) != id) return 11;
+    dag_for_each_successor(d, t, i, j, k, [&](int sid) {
+      if (sid < 0 || sid >= n) bad = 1;
+      else indeg[sid]++;
+    });
+    if (bad) return 2;
+  }
+  for (int id = 0; id < n; id++) {
+    int i, j, k;
+    int t = dag_decode(d, id, &i, &j, &k);
+    if (indeg[id] != dag_indegree(t, i, j, k)) return 3;
+    deps[id] = indeg[id];
+  }
+  // random-order execution of the counter protocol
+  std::vector<int> ready;
+  for (int id = 0; id < n; id++) if (deps[id] == 0) ready.push_back(id);
+  unsigned st = seed * 2654435761u + 12345u;
+  // tile version counters: number of writes each tile has seen
+  std::vector<int> ver((size_t)p * q, 0);
+  int executed = 0;
+  while (!ready.empty()) {
+    st = st * 1664525u + 1013904223u;
+    size_t pick = st % ready.size();
+    int id = ready[pick];
+    ready[pick] = ready.back();
+    ready.pop_back();
+    int i, j, k;
+    int t = dag_decode(d, id, &i, &j, &k);
+    // Algorithm 4 writer chain: before step k's write, tile (a,c) has been
+    // written once per earlier step that touched it (min(a,c,k) steps), plus
+    // for R_kj / R_kk the earlier i of this step.
+    auto expect = [&](int a, int c2) { return std::min(std::min(a, c2), k); };
+    if (t == 0) { if (ver[(size_t)k * p + k] != expect(k, k)) return 4; ver[(size_t)k * p + k]++; }
+    if (t == 1) {
+      if (ver[(size_t)j * p + k] != expect(k, j)) return 5;
+      if (ver[(size_t)k * p + k] < k + 1) return 12;                  // reads Y_kk after GEQRT(k)
+      ver[(size_t)j * p + k]++;
+    }
+    if (t == 2) {
+      if (ver[(size_t)k * p + i] != expect(i, k)) return 6;
+      ver[(size_t)k * p + i]++;
+      if (ver[(size_t)k * p + k] != k + 1 + (i - k - 1)) return 7;   // R_kk after GEQRT and i-k-1 TSQRTs
+      ver[(size_t)k * p + k]++;
+    }
+    if (t == 3) {
+      if (ver[(size_t)k * p + i] != k + 1) return 13;                 // reads Y~_ik after TSQRT(i,k)
+      if (ver[(size_t)j * p + i] != expect(i, j)) return 8;
+      ver[(size_t)j * p + i]++;
+      if (ver[(size_t)j * p + k] != k + 1 + (i - k - 1)) return 9;   // R_kj after LARFB and i-k-1 updates
+      ver[(size_t)j * p + k]++;
+    }
+    order_done[id] = executed++;
+    dag_for_each_successor(d, t, i, j, k, [&](int sid) {
+      if (--deps[sid] == 0) ready.push_back(sid);
+    });
+  }
+  if (executed != n) return 10;
+  return 0;
+}

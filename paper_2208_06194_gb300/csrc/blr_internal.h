@@ -1,0 +1,96 @@
+// Internal host/device definitions of the BLR-QR library.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stddef.h>
+#include "blr.h"
+
+// CTA shape shared by every kernel in the library.
+#define BLR_NT 256                    // threads per CTA
+#define BLR_NWARP (BLR_NT / 32)
+#define BLR_NB 32                     // reflectors per compact-WY block (inner blocking)
+#define BLR_CW 64                     // column chunk of a block-reflector apply
+#define BLR_RB 64                     // row block staged in shared memory
+#define BLR_BMAX 512                  // largest supported tile size
+#define BLR_SLAB_B2 20                // scratch slab per CTA, in units of b*b doubles
+
+// Shared-memory carve-out (doubles) used by the task bodies.
+#define BLR_PNL_LD_MAX (BLR_BMAX + 1)
+#define BLR_SM_PNL (BLR_PNL_LD_MAX * BLR_NB)          // panel: up to 513 x 32
+#define BLR_SM_CS ((BLR_RB + 1) * BLR_CW)             // staged C block
+#define BLR_SM_Z (BLR_NB * BLR_CW)                    // Z = Y^T C chunk
+#define BLR_SM_W (BLR_NB * BLR_CW)                    // W = T^T Z chunk
+#define BLR_SM_T (BLR_NB * BLR_NB)                    // one T block
+#define BLR_SM_RP (BLR_NB * BLR_NB)                   // R panel block (TSQRT)
+#define BLR_SM_MISC 1408                              // reductions, scalars, taus, norms, perms
+#define BLR_SM_DOUBLES (BLR_SM_PNL + BLR_SM_CS + BLR_SM_Z + BLR_SM_W + BLR_SM_T + BLR_SM_RP + BLR_SM_MISC)
+#define BLR_SMEM_BYTES (BLR_SM_DOUBLES * 8)
+
+// Task types of the tile DAG (Algorithm 4).
+#define TASK_GEQRT 0
+#define TASK_LARFB 1
+#define TASK_TSQRT 2
+#define TASK_TPMQRT 3
+
+#define BLR_NQ 3                      // ready queues by priority
+
+// Device status bits (combined with atomicOr).
+#define ST_TIMEOUT 1
+#define ST_NUMERIC 2
+#define ST_RANK 4
+#define ST_BADTASK 8
+
+struct blr_matrix {
+  int m, n, b, p, q, cap;
+  double* tiles;   // p*q blocks of b*b doubles, block (i,j) at (j*p+i)*b*b
+  int* rank;       // p*q, -1 = dense
+  size_t bytes;
+};
+
+struct blr_factor {
+  blr_matrix a;    // in-place R / Y~ storage
+  double* t;       // T blocks: for each (i,k), i >= k, 32 x b doubles
+  long long* toff; // host: offset (in units of 32*b doubles) of column k's first T block
+  int nt;          // number of T blocks
+  blr_opts opts;
+  double flops[5];
+  long long tasks[4];
+  double seconds;
+};
+
+// Parameters of the persistent scheduler kernel.
+struct SchedParams {
+  int p, q, b, cap, dense_rank, precision;
+  double rec_tol;
+  double* tiles;
+  int* rank;
+  double* t;
+  const long long* toff_dev;    // per k, offset in T blocks
+  const int* off_larfb;          // per k: first task id of LARFB(k, .)
+  const int* off_tsqrt;          // per k
+  const int* off_tpmqrt;         // per k
+  int n_tasks;
+  int* deps;
+  int* qbuf;                     // BLR_NQ * n_tasks
+  int* qhead;                    // BLR_NQ, spaced by 32 ints
+  int* qtail;
+  int* done;
+  int* status;
+  unsigned long long* progress_ns;
+  long long watchdog_ns;
+  double* scratch;
+  size_t slab;                   // doubles per CTA
+  double* flops;                 // 4 counters
+  unsigned long long* ntask;     // 4 counters
+};
+
+// host helpers (blr_api.cu)
+void blr_set_error(const char* fmt, ...);
+int blr_cuda_check(cudaError_t e, const char* what);
+int blr_num_sms();
+
+// kernel launchers implemented in the .cu files
+int blr_launch_factor(blr_factor* f, const blr_opts* o, cudaStream_t st);
+int blr_compress_impl(const double* a_dev, int lda, const double* x_dev, const double* y_dev,
+                      int dim, int kernel_id, const double* scale_dev, int m, int n,
+                      const blr_opts* o, blr_matrix* out, cudaStream_t st);

@@ -1,0 +1,349 @@
+// Uses of the factor: Q^T B and Q B (Algorithm 5, reflectors applied exactly
+// in factorization order or its reverse), R X, A~ X, and least squares
+// x = R^{-1} (Q^T B)(1:n) with optional refinement (QR for least squares,
+// Section 1).  Every kernel gives each CTA a group of right-hand-side
+// columns; the reflector sequence is applied in order inside the CTA.
+#include <cstdio>
+#include <vector>
+#include "blr_device.cuh"
+
+namespace {
+
+constexpr int kColsPerCta = 8;
+
+struct FactorView {
+  int p, q, b, cap;
+  const double* tiles;
+  const int* rank;
+  const double* t;
+  const long long* toff;   // device, per k
+  int* status;
+  double* scratch;
+  size_t slab;
+};
+
+__device__ __forceinline__ const double* ftile(const FactorView& F, int i, int j) {
+  return F.tiles + ((size_t)j * F.p + i) * (size_t)F.b * F.b;
+}
+__device__ __forceinline__ const double* ft(const FactorView& F, int i, int k) {
+  return F.t + (size_t)(F.toff[k] + (i - k)) * BLR_NB * F.b;
+}
+
+// [Ck; Ci] <- Q_ik^T [Ck; Ci] (trans) or Q_ik [Ck; Ci]; Ck, Ci are b x nc, ld ldc.
+__device__ void apply_ts_tile(const FactorView& F, int i, int k, double* Ck, double* Ci, long long ldc,
+                              int nc, bool trans, double* scr, Ctx& c) {
+  const int b = F.b;
+  const int r = __ldcg(F.rank + (size_t)k * F.p + i);
+  const double* Y = ftile(F, i, k);
+  const double* T = ft(F, i, k);
+  if (r == 0) return;
+  if (r < 0) {
+    apply_ts_reflector(colmajor(const_cast<double*>(Y), b), b, b, T, Ck, ldc, colmajor(Ci, (int)ldc), nc,
+                       trans, c);
+    return;
+  }
+  double* Pm = scr;
+  double* P0 = scr + (size_t)r * nc;
+  gemm(r, nc, b, 1.0, Y, b, true, Ci, ldc, false, 0.0, Pm, r, c);
+  copy_mat(P0, r, Pm, r, r, nc);
+  __syncthreads();
+  apply_ts_reflector(rowmajor(const_cast<double*>(Y) + (size_t)b * F.cap, b), r, b, T, Ck, ldc,
+                     colmajor(Pm, r), nc, trans, c);
+  for (int e = threadIdx.x; e < r * nc; e += BLR_NT) Pm[e] -= P0[e];
+  __syncthreads();
+  gemm(b, nc, r, 1.0, Y, b, false, Pm, r, false, 1.0, Ci, ldc, c);
+}
+
+__global__ void __launch_bounds__(BLR_NT, 1) k_apply_q(FactorView F, double* B, long long ldb, int nrhs,
+                                                        int trans) {
+  extern __shared__ double smem[];
+  Ctx c;
+  c.s = sm_carve(smem);
+  c.status = F.status;
+  c.fma = 0.0;
+  const int c0 = blockIdx.x * kColsPerCta;
+  const int nc = min(kColsPerCta, nrhs - c0);
+  if (nc <= 0) return;
+  double* Bc = B + (size_t)c0 * ldb;
+  double* scr = F.scratch + (size_t)blockIdx.x * F.slab;
+  const int b = F.b;
+  if (trans) {
+    for (int k = 0; k < F.q; k++) {
+      apply_q(ftile(F, k, k), b, b, b, ft(F, k, k), Bc + (size_t)k * b, ldb, nc, true, c);
+      for (int i = k + 1; i < F.p; i++)
+        apply_ts_tile(F, i, k, Bc + (size_t)k * b, Bc + (size_t)i * b, ldb, nc, true, scr, c);
+    }
+  } else {
+    for (int k = F.q - 1; k >= 0; k--) {
+      for (int i = F.p - 1; i > k; i--)
+        apply_ts_tile(F, i, k, Bc + (size_t)k * b, Bc + (size_t)i * b, ldb, nc, false, scr, c);
+      apply_q(ftile(F, k, k), b, b, b, ft(F, k, k), Bc + (size_t)k * b, ldb, nc, false, c);
+    }
+  }
+}
+
+// X = R^{-1} C (n x nrhs), back substitution by block rows.
+__global__ void __launch_bounds__(BLR_NT, 1) k_solve_r(FactorView F, const double* C, long long ldc,
+                                                        double* X, long long ldx, int nrhs) {
+  extern __shared__ double smem[];
+  Ctx c;
+  c.s = sm_carve(smem);
+  c.status = F.status;
+  c.fma = 0.0;
+  const int c0 = blockIdx.x * kColsPerCta;
+  const int nc = min(kColsPerCta, nrhs - c0);
+  if (nc <= 0) return;
+  const int b = F.b;
+  double* scr = F.scratch + (size_t)blockIdx.x * F.slab;
+  double* rhs = scr;                              // b x nc
+  double* tmp = scr + (size_t)b * kColsPerCta;    // cap x nc
+  double* xs = c.s.vec;                           // nc values of the current row
+  for (int k = F.q - 1; k >= 0; k--) {
+    copy_mat(rhs, b, C + (size_t)k * b + (size_t)c0 * ldc, ldc, b, nc);
+    __syncthreads();
+    for (int j = k + 1; j < F.q; j++) {
+      const double* Rkj = ftile(F, k, j);
+      const int r = __ldcg(F.rank + (size_t)j * F.p + k);
+      const double* Xj = X + (size_t)j * b + (size_t)c0 * ldx;
+      if (r < 0) {
+        gemm(b, nc, b, -1.0, Rkj, b, false, Xj, ldx, false, 1.0, rhs, b, c);
+      } else if (r > 0) {
+        gemm(r, nc, b, 1.0, Rkj + (size_t)b * F.cap, b, true, Xj, ldx, false, 0.0, tmp, r, c);
+        gemm(b, nc, r, -1.0, Rkj, b, false, tmp, r, false, 1.0, rhs, b, c);
+      }
+    }
+    const double* Rkk = ftile(F, k, k);
+    for (int a = b - 1; a >= 0; a--) {
+      if (threadIdx.x < nc) {
+        const double d = __ldcg(Rkk + a + (size_t)a * b);
+        if (d == 0.0 || !isfinite(d)) atomicOr(F.status, ST_NUMERIC);
+        xs[threadIdx.x] = rhs[a + (size_t)threadIdx.x * b] / d;
+      }
+      __syncthreads();
+      for (int e = threadIdx.x; e < a * nc; e += BLR_NT) {
+        int row = e % a, col = e / a;
+        rhs[row + (size_t)col * b] -= __ldcg(Rkk + row + (size_t)a * b) * xs[col];
+      }
+      if (threadIdx.x < nc) rhs[a + (size_t)threadIdx.x * b] = xs[threadIdx.x];
+      __syncthreads();
+    }
+    copy_mat(X + (size_t)k * b + (size_t)c0 * ldx, ldx, rhs, b, b, nc);
+    __syncthreads();
+  }
+}
+
+// Y = A~ X (mode 0, BLR matrix, p block rows) or Y = R X (mode 1, factor).
+__global__ void __launch_bounds__(BLR_NT, 1) k_matmul(FactorView F, int mode, const double* X, long long ldx,
+                                                       double* Y, long long ldy, int nrhs) {
+  extern __shared__ double smem[];
+  Ctx c;
+  c.s = sm_carve(smem);
+  c.status = F.status;
+  c.fma = 0.0;
+  const int rows = (mode == 0) ? F.p : F.q;
+  const int i = blockIdx.x % rows;
+  const int cg = blockIdx.x / rows;
+  const int c0 = cg * kColsPerCta;
+  const int nc = min(kColsPerCta, nrhs - c0);
+  if (nc <= 0) return;
+  const int b = F.b;
+  double* scr = F.scratch + (size_t)blockIdx.x * F.slab;
+  double* acc = scr;                        // b x nc
+  double* tmp = scr + (size_t)b * kColsPerCta;
+  double* rkk = tmp + (size_t)b * kColsPerCta;   // b x b (mode 1)
+  zero_mat(acc, b, b, nc);
+  __syncthreads();
+  const int j0 = (mode == 0) ? 0 : i;
+  for (int j = j0; j < F.q; j++) {
+    const double* A = ftile(F, i, j);
+    const int r = __ldcg(F.rank + (size_t)j * F.p + i);
+    const double* Xj = X + (size_t)j * b + (size_t)c0 * ldx;
+    if (mode == 1 && j == i) {
+      for (int e = threadIdx.x; e < b * b; e += BLR_NT) {
+        int a = e % b, l = e / b;
+        rkk[e] = (a <= l) ? __ldcg(A + e) : 0.0;
+      }
+      __syncthreads();
+      gemm(b, nc, b, 1.0, rkk, b, false, Xj, ldx, false, 1.0, acc, b, c);
+    } else if (r < 0) {
+      gemm(b, nc, b, 1.0, A, b, false, Xj, ldx, false, 1.0, acc, b, c);
+    } else if (r > 0) {
+      gemm(r, nc, b, 1.0, A + (size_t)b * F.cap, b, true, Xj, ldx, false, 0.0, tmp, r, c);
+      gemm(b, nc, r, 1.0, A, b, false, tmp, r, false, 1.0, acc, b, c);
+    }
+  }
+  copy_mat(Y + (size_t)i * b + (size_t)c0 * ldy, ldy, acc, b, b, nc);
+}
+
+struct Scratch {
+  double* scratch = nullptr;
+  long long* toff = nullptr;
+  int* status = nullptr;
+  ~Scratch() {
+    if (scratch) cudaFree(scratch);
+    if (toff) cudaFree(toff);
+    if (status) cudaFree(status);
+  }
+};
+
+int make_view(const blr_matrix& a, const double* t, int q_for_toff, FactorView* F, Scratch* S,
+              int nctas, size_t slab, cudaStream_t st) {
+  F->p = a.p; F->q = a.q; F->b = a.b; F->cap = a.cap;
+  F->tiles = a.tiles; F->rank = a.rank; F->t = t;
+  F->slab = slab;
+  int rc = blr_cuda_check(cudaMalloc(&S->scratch, sizeof(double) * slab * nctas), "solve scratch");
+  if (rc) return rc;
+  rc = blr_cuda_check(cudaMalloc(&S->status, sizeof(int)), "solve status");
+  if (rc) return rc;
+  rc = blr_cuda_check(cudaMemsetAsync(S->status, 0, sizeof(int), st), "memset");
+  if (rc) return rc;
+  F->scratch = S->scratch;
+  F->status = S->status;
+  F->toff = nullptr;
+  if (q_for_toff > 0) {
+    std::vector<long long> toff(q_for_toff);
+    long long acc = 0;
+    for (int k = 0; k < q_for_toff; k++) { toff[k] = acc; acc += a.p - k; }
+    rc = blr_cuda_check(cudaMalloc(&S->toff, sizeof(long long) * q_for_toff), "toff");
+    if (rc) return rc;
+    rc = blr_cuda_check(cudaMemcpy(S->toff, toff.data(), sizeof(long long) * q_for_toff, cudaMemcpyHostToDevice), "toff");
+    if (rc) return rc;
+    F->toff = S->toff;
+  }
+  return BLR_OK;
+}
+
+int finish(const FactorView& F, cudaStream_t st, const char* what) {
+  int rc = blr_cuda_check(cudaStreamSynchronize(st), what);
+  if (rc) return rc;
+  int s = 0;
+  rc = blr_cuda_check(cudaMemcpy(&s, F.status, sizeof(int), cudaMemcpyDeviceToHost), what);
+  if (rc) return rc;
+  if (s & ST_NUMERIC) {
+    blr_set_error("%s: zero or non-finite diagonal entry of R", what);
+    return BLR_ERR_NUMERIC;
+  }
+  return BLR_OK;
+}
+
+int set_smem() {
+  static bool done = false;
+  if (done) return BLR_OK;
+  int rc = blr_cuda_check(cudaFuncSetAttribute(k_apply_q, cudaFuncAttributeMaxDynamicSharedMemorySize, BLR_SMEM_BYTES), "smem");
+  if (!rc) rc = blr_cuda_check(cudaFuncSetAttribute(k_solve_r, cudaFuncAttributeMaxDynamicSharedMemorySize, BLR_SMEM_BYTES), "smem");
+  if (!rc) rc = blr_cuda_check(cudaFuncSetAttribute(k_matmul, cudaFuncAttributeMaxDynamicSharedMemorySize, BLR_SMEM_BYTES), "smem");
+  if (!rc) done = true;
+  return rc;
+}
+
+int apply_q_launch(const blr_factor* f, double* B, int ldb, int nrhs, int trans, cudaStream_t st) {
+  FactorView F{};
+  Scratch S;
+  const int nct = (nrhs + kColsPerCta - 1) / kColsPerCta;
+  int rc = set_smem();
+  if (!rc) rc = make_view(f->a, f->t, f->a.q, &F, &S, nct, (size_t)2 * f->a.cap * kColsPerCta + 64, st);
+  if (rc) return rc;
+  k_apply_q<<<nct, BLR_NT, BLR_SMEM_BYTES, st>>>(F, B, ldb, nrhs, trans);
+  rc = blr_cuda_check(cudaGetLastError(), "launch k_apply_q");
+  if (rc) return rc;
+  return finish(F, st, "blr_apply_qt");
+}
+
+int solve_r_launch(const blr_factor* f, const double* C, int ldc, double* X, int ldx, int nrhs, cudaStream_t st) {
+  FactorView F{};
+  Scratch S;
+  const int nct = (nrhs + kColsPerCta - 1) / kColsPerCta;
+  int rc = set_smem();
+  if (!rc) rc = make_view(f->a, f->t, 0, &F, &S, nct, (size_t)(f->a.b + f->a.cap) * kColsPerCta + 64, st);
+  if (rc) return rc;
+  k_solve_r<<<nct, BLR_NT, BLR_SMEM_BYTES, st>>>(F, C, ldc, X, ldx, nrhs);
+  rc = blr_cuda_check(cudaGetLastError(), "launch k_solve_r");
+  if (rc) return rc;
+  return finish(F, st, "blr_lstsq");
+}
+
+int matmul_launch(const blr_matrix& a, int mode, const double* X, int ldx, double* Y, int ldy, int nrhs,
+                  cudaStream_t st) {
+  FactorView F{};
+  Scratch S;
+  const int ncg = (nrhs + kColsPerCta - 1) / kColsPerCta;
+  const int rows = mode == 0 ? a.p : a.q;
+  int rc = set_smem();
+  if (!rc) rc = make_view(a, nullptr, 0, &F, &S, rows * ncg, (size_t)2 * a.b * kColsPerCta + (size_t)a.b * a.b + 64, st);
+  if (rc) return rc;
+  k_matmul<<<rows * ncg, BLR_NT, BLR_SMEM_BYTES, st>>>(F, mode, X, ldx, Y, ldy, nrhs);
+  rc = blr_cuda_check(cudaGetLastError(), "launch k_matmul");
+  if (rc) return rc;
+  return finish(F, st, "blr_matmul");
+}
+
+__global__ void k_axpby(double* y, long long ldy, const double* x, long long ldx, int rows, int cols,
+                        double alpha, double beta) {
+  long long tot = (long long)rows * cols;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < tot; e += (long long)gridDim.x * blockDim.x) {
+    int r = (int)(e % rows), c = (int)(e / rows);
+    y[r + c * ldy] = alpha * x[r + c * ldx] + beta * y[r + c * ldy];
+  }
+}
+
+}  // namespace
+
+extern "C" int blr_apply_qt(const blr_factor* f, double* b_dev, int ldb, int nrhs, int trans, void* stream) {
+  if (!f || !b_dev) { blr_set_error("NULL argument"); return BLR_ERR_INVALID; }
+  if (ldb < f->a.m || nrhs < 0) { blr_set_error("bad ldb or nrhs"); return BLR_ERR_INVALID; }
+  if (nrhs == 0) return BLR_OK;
+  return apply_q_launch(f, b_dev, ldb, nrhs, trans ? 0 : 1, (cudaStream_t)stream);
+}
+
+extern "C" int blr_apply_r(const blr_factor* f, const double* x_dev, int ldx, double* y_dev, int ldy, int nrhs,
+                           void* stream) {
+  if (!f || !x_dev || !y_dev) { blr_set_error("NULL argument"); return BLR_ERR_INVALID; }
+  if (ldx < f->a.n || ldy < f->a.n || nrhs < 0) { blr_set_error("bad leading dimension"); return BLR_ERR_INVALID; }
+  if (nrhs == 0) return BLR_OK;
+  return matmul_launch(f->a, 1, x_dev, ldx, y_dev, ldy, nrhs, (cudaStream_t)stream);
+}
+
+extern "C" int blr_matmul(const blr_matrix* a, const double* x_dev, int ldx, double* y_dev, int ldy, int nrhs,
+                          void* stream) {
+  if (!a || !x_dev || !y_dev) { blr_set_error("NULL argument"); return BLR_ERR_INVALID; }
+  if (ldx < a->n || ldy < a->m || nrhs < 0) { blr_set_error("bad leading dimension"); return BLR_ERR_INVALID; }
+  if (nrhs == 0) return BLR_OK;
+  return matmul_launch(*a, 0, x_dev, ldx, y_dev, ldy, nrhs, (cudaStream_t)stream);
+}
+
+extern "C" int blr_lstsq(const blr_factor* f, const blr_matrix* a_orig, const double* b_dev, int ldb,
+                         double* x_dev, int ldx, int nrhs, int refine_steps, void* stream) {
+  if (!f || !b_dev || !x_dev) { blr_set_error("NULL argument"); return BLR_ERR_INVALID; }
+  const int m = f->a.m, n = f->a.n;
+  if (ldb < m || ldx < n || nrhs < 0 || refine_steps < 0) { blr_set_error("bad leading dimension"); return BLR_ERR_INVALID; }
+  if (refine_steps > 0 && (!a_orig || a_orig->m != m || a_orig->n != n || a_orig->b != f->a.b)) {
+    blr_set_error("refinement needs the original BLR matrix of the same shape");
+    return BLR_ERR_INVALID;
+  }
+  if (nrhs == 0) return BLR_OK;
+  cudaStream_t st = (cudaStream_t)stream;
+  double *cbuf = nullptr, *dx = nullptr;
+  int rc = blr_cuda_check(cudaMalloc(&cbuf, sizeof(double) * (size_t)m * nrhs), "lstsq buffer");
+  if (!rc) rc = blr_cuda_check(cudaMalloc(&dx, sizeof(double) * (size_t)n * nrhs), "lstsq buffer");
+  if (!rc) rc = blr_cuda_check(cudaMemcpy2DAsync(cbuf, sizeof(double) * m, b_dev, sizeof(double) * ldb, sizeof(double) * m, nrhs, cudaMemcpyDeviceToDevice, st), "copy B");
+  if (!rc) rc = apply_q_launch(f, cbuf, m, nrhs, 1, st);
+  if (!rc) rc = solve_r_launch(f, cbuf, m, x_dev, ldx, nrhs, st);
+  for (int it = 0; it < refine_steps && !rc; it++) {
+    // r = B - A x
+    rc = matmul_launch(*a_orig, 0, x_dev, ldx, cbuf, m, nrhs, st);
+    if (!rc) {
+      k_axpby<<<256, 256, 0, st>>>(cbuf, m, b_dev, ldb, m, nrhs, 1.0, -1.0);
+      rc = blr_cuda_check(cudaGetLastError(), "axpby");
+    }
+    if (!rc) rc = apply_q_launch(f, cbuf, m, nrhs, 1, st);
+    if (!rc) rc = solve_r_launch(f, cbuf, m, dx, n, nrhs, st);
+    if (!rc) {
+      k_axpby<<<256, 256, 0, st>>>(x_dev, ldx, dx, n, n, nrhs, 1.0, 1.0);
+      rc = blr_cuda_check(cudaGetLastError(), "axpby");
+    }
+  }
+  if (!rc) rc = blr_cuda_check(cudaStreamSynchronize(st), "blr_lstsq");
+  if (cbuf) cudaFree(cbuf);
+  if (dx) cudaFree(dx);
+  return rc;
+}

@@ -93,7 +93,7 @@ def test_tsqrt_update_qr(rows):
 
 
 def test_lifted_reflector_orthogonal_iff_u_orthonormal():
-    """Eq. 24: I - [I; U Y] T [I; U Y]^T is orthogonal when U^T U = I."""
+    """Eq. 21: I - [I; U Y] T [I; U Y]^T is orthogonal when U^T U = I."""
     rng = np.random.default_rng(4)
     b, r = 10, 3
     r0 = np.triu(rng.standard_normal((b, b)))
