@@ -16,7 +16,7 @@ Low-Rank Matrices"):
 * OP1..OP4 and the rounded addition of Algorithm 6 (Section 3.1).
 * Tiled Householder QR, Algorithm 4, with the BLR tile kernels of
   Section 3.4: diagonal QR (3.4.1), apply block reflector (3.4.2), update QR
-  on [R_kk; V^T] (3.4.3, Eq. 24) and apply trapezoidal block reflector
+  on [R_kk; V^T] (3.4.3, Eq. 21) and apply trapezoidal block reflector
   (3.4.4), with a recompression after every low-rank sum (Section 3.1).
 * Left multiplication by Q and Q^T in the tiled order (Algorithm 5, read
   with the "I -" that the printed update omits).
@@ -297,7 +297,7 @@ def tsqrt(r: np.ndarray, bv: np.ndarray):
     and B = V^T (r x b, low-rank tile) or the dense tile (b x b).
 
     Reflector j is [e_j; y_j]; returns R', Y (rows(B) x b, column j = y_j)
-    and T with Q = I - [I; Y] T [I; Y]^T (Eq. 22)."""
+    and T with Q = I - [I; Y] T [I; Y]^T (Eq. 20)."""
     r = np.array(r, dtype=np.float64, copy=True)
     bv = np.array(bv, dtype=np.float64, copy=True)
     nb = r.shape[0]
