@@ -87,7 +87,8 @@ typedef struct blr_stats_t {
   double flops[5];          /* factor only: counted FP ops per task type
                                (GEQRT, LARFB, TSQRT, TPMQRT, total) */
   long long tasks[4];       /* factor only: tasks executed per type */
-  double seconds;           /* factor only: device time of the last blr_qr */
+  double task_seconds[4];   /* factor only: summed task durations per type (CTA-seconds) */
+  double seconds;           /* factor only: device time of the factorization kernel */
 } blr_stats_t;
 
 /* Fills *opts with the defaults (b = 512, tol = 1e-8, FP64). */

@@ -41,7 +41,7 @@ class Stats(ctypes.Structure):
                 ("q", ctypes.c_int), ("n_dense", ctypes.c_int), ("max_rank", ctypes.c_int),
                 ("mean_rank", ctypes.c_double), ("device_bytes", ctypes.c_longlong),
                 ("flops", ctypes.c_double * 5), ("tasks", ctypes.c_longlong * 4),
-                ("seconds", ctypes.c_double)]
+                ("task_seconds", ctypes.c_double * 4), ("seconds", ctypes.c_double)]
 
 
 _lib = None
@@ -282,6 +282,7 @@ def blr_stats(obj) -> dict:
     d = {k: getattr(s, k) for k, _ in Stats._fields_}
     d["flops"] = list(s.flops)
     d["tasks"] = list(s.tasks)
+    d["task_seconds"] = list(s.task_seconds)
     return d
 
 

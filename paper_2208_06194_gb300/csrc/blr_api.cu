@@ -281,6 +281,7 @@ extern "C" int blr_stats(const void* handle, int handle_is_factor, blr_stats_t* 
     const blr_factor* f = (const blr_factor*)handle;
     for (int t = 0; t < 5; t++) out->flops[t] = f->flops[t];
     for (int t = 0; t < 4; t++) out->tasks[t] = f->tasks[t];
+    for (int t = 0; t < 4; t++) out->task_seconds[t] = f->task_seconds[t];
     out->seconds = f->seconds;
   }
   return BLR_OK;

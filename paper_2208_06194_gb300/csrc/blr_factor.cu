@@ -95,9 +95,16 @@ __device__ void ts_panel_qr(double* Rp, double* Bp, int ldb, int ry, int w, doub
 // ---------------------------------------------------------------------------
 // Rounded addition (Algorithm 6) for C = Uf H0^T where H has already been
 // QR-factored in place (R_H in its top s x s, reflectors below, T blocks TH):
-// QR(Uf), M = R_U R_H^T, SVD(M) by one-sided Jacobi, keep the first r_eps
-// columns: U_C = Q_U u_r, V_C = Q_H (M^T u_r).  Uf is overwritten.  A result
-// with rank > dense_rank is written as the dense product Uf0 H0^T.
+// QR(Uf) = Q_U R_U, core M = R_U R_H^T (s x s), then a truncated
+// column-pivoted QR of the core, M P = Q_M R_M, stopped at the smallest r
+// with ||R_M(r:,r:)||_F <= eps ||M||_F.  Because ||C - C_r||_F equals the
+// core's truncation error, the result meets Algorithm 6's bound
+// ||C - U_C V_C^T||_F <= eps ||C||_F; U_C = Q_U Q_M [I_r; 0] is orthonormal
+// and V_C = Q_H [P R_M(0:r,:)^T; 0].  (Algorithm 6 truncates the core's SVD;
+// the pivoted QR reaches the same error bound in O(s^2 r) work instead of
+// O(s^3) per Jacobi sweep, with a rank that can exceed the optimal one by a
+// few.)  Uf is overwritten.  A result whose rank would exceed dense_rank is
+// written as the dense product Uf0 H0^T.
 // ---------------------------------------------------------------------------
 __device__ void recompress_side(TaskEnv& env, double* Uf, int ldu, const double* H, const double* TH,
                                 const double* H0, int s, double* dest, int* dest_rank, Ctx& c) {
@@ -123,28 +130,18 @@ __device__ void recompress_side(TaskEnv& env, double* Uf, int ldu, const double*
     RH[e] = (a <= l) ? ldg(H + a + (size_t)l * b) : 0.0;
   }
   __syncthreads();
-  double* M0 = env.alloc((size_t)s * s);
-  gemm(s, s, s, 1.0, RU, s, false, RH, s, true, 0.0, M0, s, c);
-  // Jacobi on a copy of M (shared memory when it fits)
-  double* X;
-  int ldx;
-  if (s <= 126) {
-    X = c.s.pnl;
-    ldx = s | 1;
-  } else {
-    X = env.alloc((size_t)s * s);
-    ldx = s;
-  }
-  for (int e = threadIdx.x; e < s * s; e += BLR_NT) {
-    int a = e % s, l = e / s;
-    X[a + l * ldx] = M0[e];
-  }
+  double* M = env.alloc((size_t)s * s);
+  gemm(s, s, s, 1.0, RU, s, false, RH, s, true, 0.0, M, s, c);
+  double part = 0.0;
+  for (int e = threadIdx.x; e < s * s; e += BLR_NT) part += M[e] * M[e];
+  const double nrm2 = block_sum(part, c.s.red);
+  const double tol2 = P.rec_tol * P.rec_tol * nrm2;
+  double* tauM = env.alloc((size_t)s);
+  int* perm = c.s.ivec;
+  const int r = qrcp(M, s, s, s, tol2, P.dense_rank, perm, tauM, c.s.flag + 2, c);
+  const int over = c.s.flag[2];
   __syncthreads();
-  double* sig = c.s.vec;
-  int* order = c.s.ivec;
-  jacobi_svd(X, ldx, s, sig, order, c);
-  const int r = trunc_rank(sig, order, s, P.rec_tol, c);
-  if (r > P.dense_rank) {
+  if (over) {
     // dense fallback: the exact sum
     gemm(b, b, s, 1.0, U0, b, false, H0, b, true, 0.0, dest, b, c);
     __syncthreads();
@@ -153,22 +150,20 @@ __device__ void recompress_side(TaskEnv& env, double* Uf, int ldu, const double*
     env.used = mark;
     return;
   }
-  // u_r (s x r) and v_r sigma_r = M^T u_r
-  double* Ub = env.alloc((size_t)s * (r > 0 ? r : 1));
-  for (int e = threadIdx.x; e < s * r; e += BLR_NT) {
-    int a = e % s, l = e / s;
-    int col = order[l];
-    Ub[e] = X[a + col * ldx] / sig[col];
-  }
-  __syncthreads();
-  double* CU = env.alloc((size_t)b * (r > 0 ? r : 1));
-  double* CV = env.alloc((size_t)b * (r > 0 ? r : 1));
   if (r > 0) {
+    double* CU = env.alloc((size_t)b * r);
+    double* CV = env.alloc((size_t)b * r);
     zero_mat(CU, b, b, r);
     zero_mat(CV, b, b, r);
     __syncthreads();
-    copy_mat(CU, b, Ub, s, s, r);
-    gemm(s, r, s, 1.0, M0, s, true, Ub, s, false, 0.0, CV, b, c);
+    for (int l = threadIdx.x; l < r; l += BLR_NT) CU[l + (size_t)l * b] = 1.0;
+    // V part: P R_M(0:r,:)^T
+    for (int e = threadIdx.x; e < s * r; e += BLR_NT) {
+      int cc = e % s, l = e / s;
+      CV[perm[cc] + (size_t)l * b] = (cc >= l) ? M[l + (size_t)cc * s] : 0.0;
+    }
+    __syncthreads();
+    apply_q_unblocked(M, s, s, r, tauM, CU, b, r, false, c);   // Q_M [I_r; 0] in the top s rows
     apply_q(Uf, ldu, b, s, TU, CU, b, r, false, c);
     apply_q(H, b, b, s, TH, CV, b, r, false, c);
     copy_mat(dest, b, CU, b, b, r);
@@ -494,6 +489,7 @@ __global__ void __launch_bounds__(BLR_NT, 1) k_factor(SchedParams P) {
     if (task < 0) break;
     int i, j, k;
     const int type = dag_decode(d, task, &i, &j, &k);
+    const unsigned long long t_start = gtimer();
     c.fma = 0.0;
     env.used = 0;
     env.overflow = false;
@@ -520,6 +516,7 @@ __global__ void __launch_bounds__(BLR_NT, 1) k_factor(SchedParams P) {
       });
       atomicAdd(P.flops + type, 2.0 * c.fma);
       atomicAdd(P.ntask + type, 1ull);
+      atomicAdd(P.tns + type, gtimer() - t_start);
       atomicExch(P.progress_ns, gtimer());
       __threadfence();
       atomicAdd(P.done, 1);
@@ -561,7 +558,7 @@ int blr_launch_factor(blr_factor* f, const blr_opts* o, cudaStream_t st) {
                o_qh = take(sizeof(int) * 32 * BLR_NQ), o_qt = take(sizeof(int) * 32 * BLR_NQ),
                o_done = take(sizeof(int)), o_status = take(sizeof(int)),
                o_prog = take(sizeof(unsigned long long)), o_flops = take(sizeof(double) * 4),
-               o_ntask = take(sizeof(unsigned long long) * 4);
+               o_ntask = take(sizeof(unsigned long long) * 4), o_tns = take(sizeof(unsigned long long) * 4);
   char* base = nullptr;
   double* scratch = nullptr;
   if (cudaMalloc(&base, bytes) != cudaSuccess) { blr_set_error("blr_qr: out of device memory (scheduler state)"); return BLR_ERR_OOM; }
@@ -594,6 +591,7 @@ int blr_launch_factor(blr_factor* f, const blr_opts* o, cudaStream_t st) {
   P.slab = slab;
   P.flops = (double*)(base + o_flops);
   P.ntask = (unsigned long long*)(base + o_ntask);
+  P.tns = (unsigned long long*)(base + o_tns);
 
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   do {
@@ -621,13 +619,19 @@ int blr_launch_factor(blr_factor* f, const blr_opts* o, cudaStream_t st) {
     f->seconds = ms * 1e-3;
     int status = 0, done = 0;
     double fl[4];
-    unsigned long long nt[4];
+    unsigned long long nt[4], tns[4];
+    cudaMemcpy(tns, P.tns, sizeof(tns), cudaMemcpyDeviceToHost);
     cudaMemcpy(&status, P.status, sizeof(int), cudaMemcpyDeviceToHost);
     cudaMemcpy(&done, P.done, sizeof(int), cudaMemcpyDeviceToHost);
     cudaMemcpy(fl, P.flops, sizeof(fl), cudaMemcpyDeviceToHost);
     cudaMemcpy(nt, P.ntask, sizeof(nt), cudaMemcpyDeviceToHost);
     f->flops[4] = 0;
-    for (int t = 0; t < 4; t++) { f->flops[t] = fl[t]; f->flops[4] += fl[t]; f->tasks[t] = (long long)nt[t]; }
+    for (int t = 0; t < 4; t++) {
+      f->flops[t] = fl[t];
+      f->flops[4] += fl[t];
+      f->tasks[t] = (long long)nt[t];
+      f->task_seconds[t] = tns[t] * 1e-9;
+    }
     if (status & ST_TIMEOUT) { blr_set_error("blr_qr: scheduler watchdog expired (%d of %d tasks done)", done, n_tasks); rc = BLR_ERR_TIMEOUT; break; }
     if (status & ST_NUMERIC) { blr_set_error("blr_qr: non-finite Householder coefficient"); rc = BLR_ERR_NUMERIC; break; }
     if (status & ST_RANK) { blr_set_error("blr_qr: scratch slab exceeded"); rc = BLR_ERR_RANK_OVERFLOW; break; }

@@ -55,6 +55,7 @@ struct blr_factor {
   blr_opts opts;
   double flops[5];
   long long tasks[4];
+  double task_seconds[4];
   double seconds;
 };
 
@@ -82,6 +83,7 @@ struct SchedParams {
   size_t slab;                   // doubles per CTA
   double* flops;                 // 4 counters
   unsigned long long* ntask;     // 4 counters
+  unsigned long long* tns;       // 4 counters: summed task durations (ns)
 };
 
 // host helpers (blr_api.cu)
