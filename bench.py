@@ -1,0 +1,377 @@
+"""Benchmark: seconds of one tiled BLR-QR factorization (blr_qr) of the
+65536 x 32768 Yukawa kernel matrix (b = 512), with the fraction of the
+roofline reached by the factorization kernel, the residual and
+orthogonality of the result, an end-to-end number through host buffers,
+and the CPU oracle timed on a bounded sample.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--precision fp64|mixed] [--tol 1e-6] [--size full|small]
+
+N > 1 runs N independent replicas (one per GPU, launched by torchrun); the
+single-matrix factorization does not shard.  Prints one JSON line on rank 0.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "BLR-QR sec & %roofline at 65k x 32k; mixed vs FP64 GPU at stated ||A-QR||/||A||"
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+# FP64 ALU peak for the roofline: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz
+# (the nominal 1.25 TFLOP/s FP64 of GB300); FP32 SIMT: 152 x 128 x 2 x 2.07 GHz.
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+
+SIZES = {
+    "full": dict(m=65536, n=32768, b=512, seed_x=301, seed_y=302),
+    "small": dict(m=8192, n=4096, b=512, seed_x=301, seed_y=302),
+}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--tol", type=float, default=1e-6)
+    ap.add_argument("--dense-rank", type=int, default=128)
+    ap.add_argument("--size", default="full", choices=list(SIZES))
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--compare-fp64", action="store_true",
+                    help="also time one FP64 factorization for the mixed-vs-FP64 comparison")
+    return ap.parse_args()
+
+
+# ----------------------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi clock / throttle samples during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu: int):
+        self.gpu = gpu
+        self.proc = None
+        self.lines: list[str] = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------- helpers
+def kernel_matrix_times(pr, z, torch, dev):
+    """A Z for the uncompressed kernel matrix, evaluated on the GPU in row
+    blocks (check only; not part of the timed path)."""
+    x = torch.from_numpy(pr.x).to(dev)
+    y = torch.from_numpy(pr.y).to(dev)
+    out = torch.empty((pr.m, z.shape[1]), dtype=torch.float64, device=dev)
+    for r0 in range(0, pr.m, 2048):
+        d = torch.cdist(x[:, r0:r0 + 2048].T, y.T)
+        a = torch.exp(-d) / (d + 1e-3)
+        out[r0:r0 + 2048] = a @ z
+    return out
+
+
+def probes(blr, fac, a_clone, pr, torch, dev, k=16, seed=5):
+    """Res against A~ and A and Orth, estimated with k Gaussian probes:
+    E||M Z||_F^2 = k ||M||_F^2 for Z with N(0,1) entries."""
+    g = torch.Generator(device="cpu").manual_seed(seed)
+    m, n = pr.m, pr.n
+    z = torch.randn((n, k), generator=g, dtype=torch.float64)
+    zf = blr.to_fortran(z)
+    rz = blr.blr_apply_r(fac, zf)
+    qrz = blr.fortran_empty(m, k)
+    qrz.zero_()
+    qrz[:n] = rz
+    blr.blr_apply_qt(fac, qrz, trans=1)
+    atz = blr.blr_matmul(a_clone, zf)
+    az = kernel_matrix_times(pr, z.to(dev), torch, dev)
+    res_at = float(torch.linalg.norm(qrz - atz) / torch.linalg.norm(atz))
+    res_a = float(torch.linalg.norm(qrz - az) / torch.linalg.norm(az))
+    qz = blr.fortran_empty(m, k)
+    qz.zero_()
+    qz[:n] = zf
+    blr.blr_apply_qt(fac, qz, trans=1)
+    blr.blr_apply_qt(fac, qz, trans=0)
+    orth = float(torch.linalg.norm(qz[:n] - zf) / np.sqrt(k) / np.sqrt(n)) if k else None
+    return res_a, res_at, orth
+
+
+_SAMPLE = {}
+
+
+def cpu_baseline(pr_args, tol):
+    """The oracle as it stands on the host cores, on a bounded sample: the
+    leading 16 x 2 tiles of the same matrix (compressed once by the oracle,
+    not timed), factored by the oracle's Algorithm 4 with per-task timers;
+    the mean time per task type is scaled by the task counts of the full
+    factorization."""
+    from oracle import blr_qr as O
+    from paper_2208_06194_gb300 import workloads as W
+    b = pr_args["b"]
+    ps, qs = 16, 2
+    key = (tuple(sorted(pr_args.items())), tol)
+    if key not in _SAMPLE:
+        pr = W.yukawa3d(pr_args["m"], pr_args["n"], b, pr_args["seed_x"], pr_args["seed_y"])
+        _SAMPLE[key] = O.compress(pr.tile, ps, qs, b, eps=tol)
+    sub = _SAMPLE[key]
+    times = {"geqrt": [], "larfb": [], "tsqrt": [], "tpmqrt": []}
+
+    def timed(name, fn):
+        def w(*a, **k):
+            t0 = time.perf_counter()
+            out = fn(*a, **k)
+            times[name].append(time.perf_counter() - t0)
+            return out
+        return w
+
+    saved = (O.geqrt, O.larfb, O.tsqrt, O.tpmqrt)
+    O.geqrt, O.larfb, O.tsqrt, O.tpmqrt = (timed("geqrt", O.geqrt), timed("larfb", O.larfb),
+                                           timed("tsqrt", O.tsqrt), timed("tpmqrt", O.tpmqrt))
+    t0 = time.perf_counter()
+    try:
+        O.blr_qr(sub, tol)
+    finally:
+        O.geqrt, O.larfb, O.tsqrt, O.tpmqrt = saved
+    wall = time.perf_counter() - t0
+    p, q = pr_args["m"] // b, pr_args["n"] // b
+    counts = {"geqrt": q, "larfb": q * (q - 1) // 2,
+              "tsqrt": sum(p - k - 1 for k in range(q)),
+              "tpmqrt": sum((p - k - 1) * (q - k - 1) for k in range(q))}
+    est = sum(counts[t] * (statistics.mean(v) if v else 0.0) for t, v in times.items())
+    try:
+        cores = len(os.sched_getaffinity(0))
+    except AttributeError:
+        cores = os.cpu_count()
+    return {"value": est, "unit": "s", "cores": cores, "kind": "oracle",
+            "sample": (f"oracle Algorithm 4 on the leading {ps}x{qs} tiles of the same matrix "
+                       f"({wall:.1f} s wall; tasks timed: " +
+                       ", ".join(f"{k} {len(v)}" for k, v in times.items()) +
+                       "); mean time per task type x task counts of the full factorization"),
+            "threads": os.environ.get("OMP_NUM_THREADS", "numpy default")}
+
+
+# ----------------------------------------------------------------------------- main
+def run_reference(args, rank, world):
+    """Reference arm: the oracle (the only reference there is) on the host."""
+    if rank != 0:
+        return
+    res = []
+    for _ in range(args.warmup + args.steps):
+        res.append(cpu_baseline(SIZES[args.size], args.tol))
+    vals = [r["value"] for r in res[args.warmup:]]
+    v = statistics.median(vals)
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": v * 1e3,
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": workload_name(args), "global_batch": 1},
+            "cpu_baseline": {k: res[-1][k] for k in ("kind", "cores", "sample")} | {"value": v, "unit": "s"},
+            "e2e": {"value": v, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def workload_name(args):
+    s = SIZES[args.size]
+    return (f"yukawa3d {s['m']}x{s['n']} b={s['b']} tol={args.tol:g} RCB-ordered points "
+            f"seeds {s['seed_x']}/{s['seed_y']}")
+
+
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", str(args.gpus)))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    import torch
+    import torch.distributed as dist
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        dist.init_process_group("nccl")
+    from paper_2208_06194_gb300 import blr
+    from paper_2208_06194_gb300 import workloads as W
+    s = SIZES[args.size]
+    pr = W.yukawa3d(s["m"], s["n"], s["b"], s["seed_x"] + 1000 * rank, s["seed_y"] + 1000 * rank)
+    prec = blr.BLR_PREC_MIXED if args.precision == "mixed" else blr.BLR_PREC_FP64
+    opts = blr.blr_opts_default(b=s["b"], tol=args.tol, precision=prec, dense_rank=args.dense_rank)
+    a0 = blr.blr_compress_kernel(pr.x, pr.y, "yukawa3d", opts)
+    st_a = blr.blr_stats(a0)
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def one_step(o):
+        a = blr.blr_matrix_clone(a0)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        f = blr.blr_qr(a, o)
+        e1.record(stream)
+        e1.synchronize()
+        return f, e0.elapsed_time(e1) * 1e-3
+
+    for _ in range(args.warmup):
+        f, _t = one_step(opts)
+        f.destroy()
+    barrier()
+    clocks = ClockSampler(local)
+    clocks.start()
+    times, kern, fac = [], [], None
+    for it in range(args.steps):
+        if fac is not None:
+            fac.destroy()
+        fac, t = one_step(opts)
+        times.append(t)
+        kern.append(blr.blr_stats(fac)["seconds"])
+    barrier()
+    clk = clocks.stop()
+    st = blr.blr_stats(fac)
+    t_step = statistics.median(times)
+    if world > 1:
+        tt = torch.tensor([t_step], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_step = float(tt.item())
+    res_a, res_at, orth = probes(blr, fac, a0, pr, torch, dev)
+    fac.destroy()
+
+    # FP64 comparison at the same tolerance (mixed runs only)
+    fp64 = None
+    if args.compare_fp64 and prec == blr.BLR_PREC_MIXED:
+        o64 = blr.blr_opts_default(b=s["b"], tol=args.tol, precision=blr.BLR_PREC_FP64,
+                                   dense_rank=args.dense_rank)
+        f64, t64 = one_step(o64)
+        r64 = probes(blr, f64, a0, pr, torch, dev)
+        st64 = blr.blr_stats(f64)
+        fp64 = {"seconds": t64, "res_A": r64[0], "res_At": r64[1], "orth": r64[2],
+                "gflops_counted": st64["flops"][4] / 1e9}
+        f64.destroy()
+
+    # end to end through host buffers: import (H2D) + blr_qr + export (D2H)
+    e2e = None
+    if not args.no_e2e:
+        ranks_h, tiles_h = blr.blr_matrix_export(a0)
+        pin_t = torch.from_numpy(tiles_h).pin_memory()
+        pin_r = torch.from_numpy(ranks_h).pin_memory()
+        out_t = torch.empty_like(pin_t).pin_memory()
+        out_r = torch.empty_like(pin_r).pin_memory()
+        nt_blocks = sum(pr.m // s["b"] - k for k in range(pr.n // s["b"]))
+        out_T = torch.empty(nt_blocks * 32 * s["b"], dtype=torch.float64).pin_memory()
+        barrier()
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        a = blr.blr_matrix_import(pr.m, pr.n, s["b"], pin_r.numpy(), pin_t.numpy())
+        f = blr.blr_qr(a, opts)
+        blr.lib().blr_matrix_export(f.handle, 1, out_r.numpy().ctypes.data_as(blr._IP),
+                                    out_t.numpy().ctypes.data_as(blr._DP), blr._stream(None))
+        blr.lib().blr_factor_export_t(f.handle, out_T.numpy().ctypes.data_as(blr._DP), blr._stream(None))
+        t1.record(stream)
+        t1.synchronize()
+        f.destroy()
+        e2e_s = t0.elapsed_time(t1) * 1e-3
+        h2d = pin_t.numel() * 8 + pin_r.numel() * 4
+        d2h = out_t.numel() * 8 + out_r.numel() * 4 + out_T.numel() * 8
+        e2e = {"value": e2e_s / max(world, 1), "unit": "s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        cpu = cpu_baseline(s, args.tol)
+
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return
+    flops = st["flops"][4]
+    k_sec = statistics.median(kern)
+    achieved = flops / k_sec / 1e12
+    peak = FP64_PEAK_TFLOPS if prec == blr.BLR_PREC_FP64 else FP32_PEAK_TFLOPS
+    line = {
+        "metric": METRIC, "value": t_step / world, "unit": "s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t_step * 1e3, "higher_is_better": False,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64" if prec == 0 else "f64+f32",
+        "data": "synthetic",
+        "config": {"workload": workload_name(args), "global_batch": world, "precision": args.precision,
+                   "dense_rank": args.dense_rank, "parallelism": "replicas" if world > 1 else "single",
+                   "l2": "inputs larger than L2 (17 GB of tiles per step)"},
+        "res_A": res_a, "res_At": res_at, "orth": orth,
+        "ranks": {"before": {"n_dense": st_a["n_dense"], "mean": st_a["mean_rank"], "max": st_a["max_rank"]},
+                  "after": {"n_dense": st["n_dense"], "mean": st["mean_rank"], "max": st["max_rank"]}},
+        "kernel_seconds": k_sec,
+        "task_cta_seconds": dict(zip(["geqrt", "larfb", "tsqrt", "tpmqrt"], st["task_seconds"])),
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": achieved / peak, "traffic": None,
+                     "peak_note": ("FP64 ALU nominal 1.26 TFLOP/s (152 SMs x 2 DFMA/clk x 2.07 GHz)"
+                                   if prec == 0 else "FP32 SIMT nominal (152 x 128 FMA/clk x 2.07 GHz)"),
+                     "kernel": "k_factor (persistent scheduler)", "flops_counted": flops},
+        "clocks": clk,
+        "gpu_launches": args.steps,
+        "e2e": e2e,
+        "cpu_baseline": cpu,
+        "fp64": fp64,
+    }
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,8 +1,12 @@
-// CTA-collective FP64 building blocks of the BLR-QR kernels.
+// CTA-collective building blocks of the BLR-QR kernels.
 //
 // Every routine is called by all BLR_NT threads of a CTA, starts and ends
 // with a barrier, and works on column-major matrices (element (r,c) at
-// p[r + c*ld]).  Global operands that other CTAs may have written during a
+// p[r + c*ld]).  Templates separate the arithmetic type S (shared-memory
+// buffers and accumulators: double for the FP64 path, float for the FP32
+// trailing updates of the mixed path) from the element types of the global
+// operands (tiles are always stored in double); values are converted once
+// when staged.  Global operands that other CTAs may have written during a
 // persistent launch are read with ld.global.cg (L2, never a stale L1 line);
 // CTA-private scratch and shared memory are read with plain loads.
 //
@@ -12,6 +16,7 @@
 // gives tau = 0.  Blocks of BLR_NB reflectors are kept in compact-WY form
 // I - Y T Y^T (Eq. 3), T built by the Schreiber-Van Loan recurrence.
 #pragma once
+#include <type_traits>
 #include "blr_internal.h"
 
 #define FULLMASK 0xffffffffu
@@ -19,8 +24,9 @@
 namespace {
 
 __device__ __forceinline__ double ldg(const double* p) { return __ldcg(p); }
+__device__ __forceinline__ float ldg(const float* p) { return __ldcg(p); }
 
-// Shared-memory carve-out.
+// Shared-memory carve-out (sizes in doubles; float users reinterpret).
 struct Sm {
   double* pnl;   // BLR_SM_PNL
   double* cs;    // staged block
@@ -42,6 +48,9 @@ struct Ctx {
   double fma;       // fused multiply-adds counted for the current task (same on all threads)
 };
 
+template <class S>
+__device__ __forceinline__ S* as(double* p) { return reinterpret_cast<S*>(p); }
+
 __device__ __forceinline__ Sm sm_carve(double* base) {
   Sm s;
   s.pnl = base;
@@ -60,36 +69,38 @@ __device__ __forceinline__ Sm sm_carve(double* base) {
   return s;
 }
 
-__device__ __forceinline__ double warp_sum(double v) {
+template <class S>
+__device__ __forceinline__ S warp_sum(S v) {
 #pragma unroll
   for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(FULLMASK, v, o);
   return v;
 }
 
 // Sum over the CTA; every thread gets the same value.
-__device__ __forceinline__ double block_sum(double v, double* red) {
+template <class S>
+__device__ __forceinline__ S block_sum(S v, double* red) {
   v = warp_sum(v);
   __syncthreads();
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = (double)v;
   __syncthreads();
   double s = 0.0;
 #pragma unroll
   for (int i = 0; i < BLR_NWARP; i++) s += red[i];
-  return s;
+  return (S)s;
 }
 
-__device__ __forceinline__ void house(double alpha, double sig2, double& beta, double& tau,
-                                      double& scale) {
-  if (sig2 == 0.0) {
+template <class S>
+__device__ __forceinline__ void house(S alpha, S sig2, S& beta, S& tau, S& scale) {
+  if (sig2 == S(0)) {
     beta = alpha;
-    tau = 0.0;
-    scale = 0.0;
+    tau = S(0);
+    scale = S(0);
     return;
   }
-  double nrm = sqrt(alpha * alpha + sig2);
-  beta = (alpha >= 0.0) ? -nrm : nrm;
+  S nrm = sqrt(alpha * alpha + sig2);
+  beta = (alpha >= S(0)) ? -nrm : nrm;
   tau = (beta - alpha) / beta;
-  scale = 1.0 / (alpha - beta);
+  scale = S(1) / (alpha - beta);
 }
 
 __device__ __forceinline__ void flag_numeric(Ctx& c, double x) {
@@ -97,63 +108,70 @@ __device__ __forceinline__ void flag_numeric(Ctx& c, double x) {
 }
 
 // ---------------------------------------------------------------------------
-// Staging between global views and shared memory.
-// A strided view: element (r,c) at p[r*sr + c*sc].
+// Strided views and staging.  View<T>: element (r,c) at p[r*sr + c*sc].
 // ---------------------------------------------------------------------------
+template <class T>
 struct View {
-  double* p;
+  T* p;
   long long sr, sc;
-  __device__ __forceinline__ double* at(int r, int c) const { return p + r * sr + c * sc; }
+  __device__ __forceinline__ T* at(int r, int c) const { return p + r * sr + c * sc; }
+  __device__ __forceinline__ View shifted(int r0, int c0) const { return View{p + r0 * sr + c0 * sc, sr, sc}; }
 };
 
-__device__ __forceinline__ View colmajor(double* p, int ld) { return View{p, 1, (long long)ld}; }
-__device__ __forceinline__ View rowmajor(double* p, int ld) { return View{p, (long long)ld, 1}; }
+template <class T>
+__device__ __forceinline__ View<T> colmajor(T* p, long long ld) { return View<T>{p, 1, ld}; }
+template <class T>
+__device__ __forceinline__ View<T> rowmajor(T* p, long long ld) { return View<T>{p, ld, 1}; }
 
-// dst (smem, column-major ldd) = src (rows x cols); coalesced along src's unit stride.
-__device__ void stage_in(double* dst, int ldd, View src, int rows, int cols) {
-  int tot = rows * cols;
+// dst (shared, column-major ldd, type S) = src (rows x cols); coalesced along src's unit stride.
+template <class S, class G>
+__device__ void stage_in(S* dst, int ldd, View<G> src, int rows, int cols) {
+  const int tot = rows * cols;
   if (src.sr == 1) {
     for (int e = threadIdx.x; e < tot; e += BLR_NT) {
       int r = e % rows, c = e / rows;
-      dst[r + c * ldd] = ldg(src.at(r, c));
+      dst[r + c * ldd] = (S)ldg(src.at(r, c));
     }
   } else {
     for (int e = threadIdx.x; e < tot; e += BLR_NT) {
       int c = e % cols, r = e / cols;
-      dst[r + c * ldd] = ldg(src.at(r, c));
+      dst[r + c * ldd] = (S)ldg(src.at(r, c));
     }
   }
 }
 
-__device__ void stage_out(View dst, const double* src, int lds, int rows, int cols) {
-  int tot = rows * cols;
+template <class S, class G>
+__device__ void stage_out(View<G> dst, const S* src, int lds, int rows, int cols) {
+  const int tot = rows * cols;
   if (dst.sr == 1) {
     for (int e = threadIdx.x; e < tot; e += BLR_NT) {
       int r = e % rows, c = e / rows;
-      *dst.at(r, c) = src[r + c * lds];
+      *dst.at(r, c) = (G)src[r + c * lds];
     }
   } else {
     for (int e = threadIdx.x; e < tot; e += BLR_NT) {
       int c = e % cols, r = e / cols;
-      *dst.at(r, c) = src[r + c * lds];
+      *dst.at(r, c) = (G)src[r + c * lds];
     }
   }
 }
 
-// Global-to-global copy / zero of a rows x cols block (column-major both).
-__device__ void copy_mat(double* dst, int ldd, const double* src, int lds, int rows, int cols) {
-  long long tot = (long long)rows * cols;
+// Global-to-global copy (with conversion) / zero of a rows x cols block.
+template <class D, class Src>
+__device__ void copy_mat(D* dst, long long ldd, const Src* src, long long lds, int rows, int cols) {
+  const long long tot = (long long)rows * cols;
   for (long long e = threadIdx.x; e < tot; e += BLR_NT) {
     int r = (int)(e % rows), c = (int)(e / rows);
-    dst[r + (long long)c * ldd] = ldg(src + r + (long long)c * lds);
+    dst[r + c * ldd] = (D)ldg(src + r + c * lds);
   }
 }
 
-__device__ void zero_mat(double* dst, int ldd, int rows, int cols) {
-  long long tot = (long long)rows * cols;
+template <class D>
+__device__ void zero_mat(D* dst, long long ldd, int rows, int cols) {
+  const long long tot = (long long)rows * cols;
   for (long long e = threadIdx.x; e < tot; e += BLR_NT) {
     int r = (int)(e % rows), c = (int)(e / rows);
-    dst[r + (long long)c * ldd] = 0.0;
+    dst[r + c * ldd] = D(0);
   }
 }
 
@@ -161,61 +179,63 @@ __device__ void zero_mat(double* dst, int ldd, int rows, int cols) {
 // Unblocked Householder QR of a panel held in shared memory (h x w, w <= 32):
 // R in the upper triangle, v_j below the diagonal, tau[j].
 // ---------------------------------------------------------------------------
-__device__ void panel_qr(double* P, int ldp, int h, int w, double* tau, Ctx& c) {
+template <class S>
+__device__ void panel_qr(S* P, int ldp, int h, int w, S* tau, Ctx& c) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  S* scal = as<S>(c.s.scal);
   __syncthreads();
   for (int j = 0; j < w && j < h; j++) {
-    double part = 0.0;
+    S part = S(0);
     for (int r = j + 1 + threadIdx.x; r < h; r += BLR_NT) {
-      double x = P[r + j * ldp];
+      S x = P[r + j * ldp];
       part += x * x;
     }
-    double sig2 = block_sum(part, c.s.red);
+    S sig2 = block_sum(part, c.s.red);
     if (threadIdx.x == 0) {
-      double beta, tj, sc;
+      S beta, tj, sc;
       house(P[j + j * ldp], sig2, beta, tj, sc);
-      flag_numeric(c, beta);
-      c.s.scal[0] = beta;
-      c.s.scal[1] = tj;
-      c.s.scal[2] = sc;
+      flag_numeric(c, (double)beta);
+      scal[0] = beta;
+      scal[1] = tj;
+      scal[2] = sc;
     }
     __syncthreads();
-    const double tj = c.s.scal[1], sc = c.s.scal[2];
+    const S tj = scal[1], sc = scal[2];
     for (int r = j + 1 + threadIdx.x; r < h; r += BLR_NT) P[r + j * ldp] *= sc;
     __syncthreads();
     for (int l = j + 1 + warp; l < w; l += BLR_NWARP) {
-      double acc = 0.0;
+      S acc = S(0);
       for (int r = j + 1 + lane; r < h; r += 32) acc += P[r + j * ldp] * P[r + l * ldp];
       acc = warp_sum(acc);
-      double wl = (__shfl_sync(FULLMASK, P[j + l * ldp], 0) + acc) * tj;
+      S wl = (__shfl_sync(FULLMASK, P[j + l * ldp], 0) + acc) * tj;
       if (lane == 0) P[j + l * ldp] -= wl;
       for (int r = j + 1 + lane; r < h; r += 32) P[r + l * ldp] -= wl * P[r + j * ldp];
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-      P[j + j * ldp] = c.s.scal[0];
+      P[j + j * ldp] = scal[0];
       tau[j] = tj;
     }
     __syncthreads();
   }
-  // zero tau for columns beyond h (cannot happen for m >= n callers)
-  for (int j = h + threadIdx.x; j < w; j += BLR_NT) tau[j] = 0.0;
+  for (int j = h + threadIdx.x; j < w; j += BLR_NT) tau[j] = S(0);
   __syncthreads();
-  double hw = (double)h * w - 0.5 * (double)w * w;
-  c.fma += 2.0 * hw * w * 0.5 + hw;
+  const double hw = (double)h * w - 0.5 * (double)w * w;
+  c.fma += hw * w + hw;
 }
 
 // T (w x w upper, ld NB) from the Gram matrix G of the reflector vectors
 // (G[a + l*NB] for a < l) and tau: T_jj = tau_j, T(0:j,j) = -tau_j T(0:j,0:j) G(0:j,j).
-__device__ void t_recur(const double* G, const double* tau, int w, double* T, Ctx& c) {
+template <class S>
+__device__ void t_recur(const S* G, const S* tau, int w, S* T, Ctx& c) {
   __syncthreads();
   if (threadIdx.x < 32) {
     const int a = threadIdx.x;
     for (int j = 0; j < BLR_NB; j++) {
-      double v = 0.0;
+      S v = S(0);
       if (j < w) {
         if (a < j) {
-          double s = 0.0;
+          S s = S(0);
           for (int cc = a; cc < j; cc++) s += T[a + cc * BLR_NB] * G[cc + j * BLR_NB];
           v = -tau[j] * s;
         } else if (a == j) {
@@ -230,35 +250,41 @@ __device__ void t_recur(const double* G, const double* tau, int w, double* T, Ct
   c.fma += (double)w * w * w / 6.0;
 }
 
+__device__ __forceinline__ void decode_pair(int e, int& a, int& l) {
+  l = 1;
+  int base = 0;
+  while (base + l <= e) { base += l; l++; }
+  a = e - base;
+}
+
 // Gram of a panel's unit-lower-trapezoidal reflectors (P from panel_qr), into G (ld NB).
-__device__ void gram_panel(const double* P, int ldp, int h, int w, double* G, Ctx& c) {
+template <class S>
+__device__ void gram_panel(const S* P, int ldp, int h, int w, S* G, Ctx& c) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   __syncthreads();
   const int npair = w * (w - 1) / 2;
   for (int e = warp; e < npair; e += BLR_NWARP) {
-    // decode e -> (a, l) with a < l
-    int l = 1, base = 0;
-    while (base + l <= e) { base += l; l++; }
-    int a = e - base;
-    double acc = 0.0;
+    int a, l;
+    decode_pair(e, a, l);
+    S acc = S(0);
     for (int r = l + 1 + lane; r < h; r += 32) acc += P[r + a * ldp] * P[r + l * ldp];
     acc = warp_sum(acc);
-    if (lane == 0) G[a + l * BLR_NB] = (l < h ? P[l + a * ldp] : 0.0) + acc;
+    if (lane == 0) G[a + l * BLR_NB] = (l < h ? P[l + a * ldp] : S(0)) + acc;
   }
   __syncthreads();
   c.fma += (double)h * w * w / 2.0;
 }
 
 // Gram of dense reflector blocks Bp (ry x w, ld ldb): G[a][l] = Bp(:,a).Bp(:,l).
-__device__ void gram_dense(const double* Bp, int ldb, int ry, int w, double* G, Ctx& c) {
+template <class S>
+__device__ void gram_dense(const S* Bp, int ldb, int ry, int w, S* G, Ctx& c) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   __syncthreads();
   const int npair = w * (w - 1) / 2;
   for (int e = warp; e < npair; e += BLR_NWARP) {
-    int l = 1, base = 0;
-    while (base + l <= e) { base += l; l++; }
-    int a = e - base;
-    double acc = 0.0;
+    int a, l;
+    decode_pair(e, a, l);
+    S acc = S(0);
     for (int r = lane; r < ry; r += 32) acc += Bp[r + a * ldb] * Bp[r + l * ldb];
     acc = warp_sum(acc);
     if (lane == 0) G[a + l * BLR_NB] = acc;
@@ -268,36 +294,39 @@ __device__ void gram_dense(const double* Bp, int ldb, int ry, int w, double* G, 
 }
 
 // ---------------------------------------------------------------------------
-// C (h x nc, global, ldc) <- (I - Y T' Y^T) C with Y the unit lower
-// trapezoidal reflectors of a panel in shared memory (P, ldp, h x w) and
-// T' = T^T (trans, applies Q^T) or T (applies Q).
+// C (h x nc, global element type G, ldc) <- (I - Y T' Y^T) C with Y the unit
+// lower trapezoidal reflectors of a panel in shared memory (P, ldp, h x w,
+// type S) and T' = T^T (trans, applies Q^T) or T (applies Q).  Products are
+// accumulated in S; the update is subtracted in G.
 // ---------------------------------------------------------------------------
-__device__ void apply_refl_panel(double* C, long long ldc, int h, int nc, const double* P, int ldp,
-                                 int w, const double* T, bool trans, Ctx& c) {
+template <class S, class G>
+__device__ void apply_refl_panel(G* C, long long ldc, int h, int nc, const S* P, int ldp, int w,
+                                 const S* T, bool trans, Ctx& c) {
   const int a = threadIdx.x & 31, grp = threadIdx.x >> 5;
-  double* Cs = c.s.cs;
+  S* Cs = as<S>(c.s.cs);
   const int ldcs = BLR_RB + 1;
-  double* Z = c.s.z;
-  double* W = c.s.w;
+  S* Z = as<S>(c.s.z);
+  S* W = as<S>(c.s.w);
+  constexpr int KPT = BLR_CW / BLR_NWARP;
   for (int c0 = 0; c0 < nc; c0 += BLR_CW) {
     const int cw = min(BLR_CW, nc - c0);
-    double acc[BLR_CW / BLR_NWARP];
+    S acc[KPT];
 #pragma unroll
-    for (int k = 0; k < BLR_CW / BLR_NWARP; k++) acc[k] = 0.0;
+    for (int k = 0; k < KPT; k++) acc[k] = S(0);
     for (int r0 = 0; r0 < h; r0 += BLR_RB) {
       const int rb = min(BLR_RB, h - r0);
       __syncthreads();
       for (int e = threadIdx.x; e < rb * cw; e += BLR_NT) {
         int rr = e % rb, ll = e / rb;
-        Cs[rr + ll * ldcs] = ldg(C + (r0 + rr) + (long long)(c0 + ll) * ldc);
+        Cs[rr + ll * ldcs] = (S)ldg(C + (r0 + rr) + (long long)(c0 + ll) * ldc);
       }
       __syncthreads();
       if (a < w) {
         for (int rr = 0; rr < rb; rr++) {
           const int row = r0 + rr;
-          const double y = (row > a) ? P[row + a * ldp] : (row == a ? 1.0 : 0.0);
+          const S y = (row > a) ? P[row + a * ldp] : (row == a ? S(1) : S(0));
 #pragma unroll
-          for (int k = 0; k < BLR_CW / BLR_NWARP; k++) {
+          for (int k = 0; k < KPT; k++) {
             int ll = grp + BLR_NWARP * k;
             if (ll < cw) acc[k] += y * Cs[rr + ll * ldcs];
           }
@@ -306,17 +335,16 @@ __device__ void apply_refl_panel(double* C, long long ldc, int h, int nc, const 
     }
     __syncthreads();
 #pragma unroll
-    for (int k = 0; k < BLR_CW / BLR_NWARP; k++) {
+    for (int k = 0; k < KPT; k++) {
       int ll = grp + BLR_NWARP * k;
-      if (a < BLR_NB && ll < BLR_CW) Z[a + ll * BLR_NB] = (a < w && ll < cw) ? acc[k] : 0.0;
+      Z[a + ll * BLR_NB] = (a < w && ll < cw) ? acc[k] : S(0);
     }
     __syncthreads();
-    // W = T^T Z (trans) or T Z
 #pragma unroll
-    for (int k = 0; k < BLR_CW / BLR_NWARP; k++) {
+    for (int k = 0; k < KPT; k++) {
       int ll = grp + BLR_NWARP * k;
       if (ll < cw && a < w) {
-        double s = 0.0;
+        S s = S(0);
         if (trans) {
           for (int cc = 0; cc <= a; cc++) s += T[cc + a * BLR_NB] * Z[cc + ll * BLR_NB];
         } else {
@@ -326,40 +354,41 @@ __device__ void apply_refl_panel(double* C, long long ldc, int h, int nc, const 
       }
     }
     __syncthreads();
-    // C -= Y W
     for (long long e = threadIdx.x; e < (long long)h * cw; e += BLR_NT) {
       int row = (int)(e % h), ll = (int)(e / h);
-      double s = 0.0;
+      S s = S(0);
       const int amax = min(w, row + 1);
       for (int aa = 0; aa < amax; aa++) {
-        const double y = (row > aa) ? P[row + aa * ldp] : 1.0;
+        const S y = (row > aa) ? P[row + aa * ldp] : S(1);
         s += y * W[aa + ll * BLR_NB];
       }
-      double* cp = C + row + (long long)(c0 + ll) * ldc;
-      *cp = ldg(cp) - s;
+      G* cp = C + row + (long long)(c0 + ll) * ldc;
+      *cp = ldg(cp) - (G)s;
     }
     __syncthreads();
   }
   c.fma += (2.0 * h * w + 0.5 * w * w) * nc;
 }
 
-// [Ct (w rows, ldt); Cb (ry x nc view)] <- (I - [I; Yb] T' [I; Yb]^T) [Ct; Cb]
-// for a block of reflectors [e_a; yb_a] (Yb in shared memory, ry x w, ldyb).
-__device__ void apply_refl_ts(double* Ct, long long ldt, View Cb, int ry, int nc,
-                              const double* Yb, int ldyb, int w, const double* T, bool trans,
-                              Ctx& c) {
+// [Ct (w rows, ldt, type GT); Cb (ry x nc view, type GB)] <-
+// (I - [I; Yb] T' [I; Yb]^T) [Ct; Cb] for a block of reflectors [e_a; yb_a]
+// (Yb in shared memory, ry x w, ldyb, type S).
+template <class S, class GT, class GB>
+__device__ void apply_refl_ts(GT* Ct, long long ldt, View<GB> Cb, int ry, int nc, const S* Yb, int ldyb,
+                              int w, const S* T, bool trans, Ctx& c) {
   const int a = threadIdx.x & 31, grp = threadIdx.x >> 5;
-  double* Cs = c.s.cs;
+  S* Cs = as<S>(c.s.cs);
   const int ldcs = BLR_RB + 1;
-  double* Z = c.s.z;
-  double* W = c.s.w;
+  S* Z = as<S>(c.s.z);
+  S* W = as<S>(c.s.w);
+  constexpr int KPT = BLR_CW / BLR_NWARP;
   for (int c0 = 0; c0 < nc; c0 += BLR_CW) {
     const int cw = min(BLR_CW, nc - c0);
-    double acc[BLR_CW / BLR_NWARP];
+    S acc[KPT];
 #pragma unroll
-    for (int k = 0; k < BLR_CW / BLR_NWARP; k++) {
+    for (int k = 0; k < KPT; k++) {
       int ll = grp + BLR_NWARP * k;
-      acc[k] = (a < w && ll < cw) ? ldg(Ct + a + (long long)(c0 + ll) * ldt) : 0.0;
+      acc[k] = (a < w && ll < cw) ? (S)ldg(Ct + a + (long long)(c0 + ll) * ldt) : S(0);
     }
     for (int r0 = 0; r0 < ry; r0 += BLR_RB) {
       const int rb = min(BLR_RB, ry - r0);
@@ -367,20 +396,20 @@ __device__ void apply_refl_ts(double* Ct, long long ldt, View Cb, int ry, int nc
       if (Cb.sr == 1) {
         for (int e = threadIdx.x; e < rb * cw; e += BLR_NT) {
           int rr = e % rb, ll = e / rb;
-          Cs[rr + ll * ldcs] = ldg(Cb.at(r0 + rr, c0 + ll));
+          Cs[rr + ll * ldcs] = (S)ldg(Cb.at(r0 + rr, c0 + ll));
         }
       } else {
         for (int e = threadIdx.x; e < rb * cw; e += BLR_NT) {
           int ll = e % cw, rr = e / cw;
-          Cs[rr + ll * ldcs] = ldg(Cb.at(r0 + rr, c0 + ll));
+          Cs[rr + ll * ldcs] = (S)ldg(Cb.at(r0 + rr, c0 + ll));
         }
       }
       __syncthreads();
       if (a < w) {
         for (int rr = 0; rr < rb; rr++) {
-          const double y = Yb[(r0 + rr) + a * ldyb];
+          const S y = Yb[(r0 + rr) + a * ldyb];
 #pragma unroll
-          for (int k = 0; k < BLR_CW / BLR_NWARP; k++) {
+          for (int k = 0; k < KPT; k++) {
             int ll = grp + BLR_NWARP * k;
             if (ll < cw) acc[k] += y * Cs[rr + ll * ldcs];
           }
@@ -389,16 +418,16 @@ __device__ void apply_refl_ts(double* Ct, long long ldt, View Cb, int ry, int nc
     }
     __syncthreads();
 #pragma unroll
-    for (int k = 0; k < BLR_CW / BLR_NWARP; k++) {
+    for (int k = 0; k < KPT; k++) {
       int ll = grp + BLR_NWARP * k;
-      if (ll < BLR_CW) Z[a + ll * BLR_NB] = (a < w && ll < cw) ? acc[k] : 0.0;
+      Z[a + ll * BLR_NB] = (a < w && ll < cw) ? acc[k] : S(0);
     }
     __syncthreads();
 #pragma unroll
-    for (int k = 0; k < BLR_CW / BLR_NWARP; k++) {
+    for (int k = 0; k < KPT; k++) {
       int ll = grp + BLR_NWARP * k;
       if (ll < cw && a < w) {
-        double s = 0.0;
+        S s = S(0);
         if (trans) {
           for (int cc = 0; cc <= a; cc++) s += T[cc + a * BLR_NB] * Z[cc + ll * BLR_NB];
         } else {
@@ -408,28 +437,26 @@ __device__ void apply_refl_ts(double* Ct, long long ldt, View Cb, int ry, int nc
       }
     }
     __syncthreads();
-    // top rows: Ct -= W
     for (int e = threadIdx.x; e < w * cw; e += BLR_NT) {
       int aa = e % w, ll = e / w;
-      double* cp = Ct + aa + (long long)(c0 + ll) * ldt;
-      *cp = ldg(cp) - W[aa + ll * BLR_NB];
+      GT* cp = Ct + aa + (long long)(c0 + ll) * ldt;
+      *cp = ldg(cp) - (GT)W[aa + ll * BLR_NB];
     }
-    // bottom rows: Cb -= Yb W
     if (Cb.sr == 1) {
       for (long long e = threadIdx.x; e < (long long)ry * cw; e += BLR_NT) {
         int rr = (int)(e % ry), ll = (int)(e / ry);
-        double s = 0.0;
+        S s = S(0);
         for (int aa = 0; aa < w; aa++) s += Yb[rr + aa * ldyb] * W[aa + ll * BLR_NB];
-        double* cp = Cb.at(rr, c0 + ll);
-        *cp = ldg(cp) - s;
+        GB* cp = Cb.at(rr, c0 + ll);
+        *cp = ldg(cp) - (GB)s;
       }
     } else {
       for (long long e = threadIdx.x; e < (long long)ry * cw; e += BLR_NT) {
         int ll = (int)(e % cw), rr = (int)(e / cw);
-        double s = 0.0;
+        S s = S(0);
         for (int aa = 0; aa < w; aa++) s += Yb[rr + aa * ldyb] * W[aa + ll * BLR_NB];
-        double* cp = Cb.at(rr, c0 + ll);
-        *cp = ldg(cp) - s;
+        GB* cp = Cb.at(rr, c0 + ll);
+        *cp = ldg(cp) - (GB)s;
       }
     }
     __syncthreads();
@@ -438,44 +465,44 @@ __device__ void apply_refl_ts(double* Ct, long long ldt, View Cb, int ry, int nc
 }
 
 // ---------------------------------------------------------------------------
-// C = alpha op(A) op(B) + beta C, all global, column-major.  beta == 0 never
-// reads C.
+// C = alpha op(A) op(B) + beta C, global operands of element types GA, GB,
+// GC, products accumulated in S.  beta == 0 never reads C.
 // ---------------------------------------------------------------------------
-__device__ void gemm(int m, int n, int k, double alpha, const double* A, long long lda, bool ta,
-                     const double* B, long long ldb, bool tb, double beta, double* C,
-                     long long ldc, Ctx& c) {
-  double* As = c.s.cs;            // 64 x 16, ld 65
-  double* Bs = c.s.cs + 65 * 16;  // 16 x 64, ld 64
+template <class S, class GA, class GB, class GC>
+__device__ void gemm(int m, int n, int k, S alpha, const GA* A, long long lda, bool ta, const GB* B,
+                     long long ldb, bool tb, S beta, GC* C, long long ldc, Ctx& c) {
+  S* As = as<S>(c.s.cs);            // 64 x 16, ld 65
+  S* Bs = as<S>(c.s.cs) + 65 * 16;  // 16 x 64, ld 64
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
   for (int tm = 0; tm < m; tm += 64) {
     for (int tn = 0; tn < n; tn += 64) {
-      double acc[4][4];
+      S acc[4][4];
 #pragma unroll
       for (int i = 0; i < 4; i++)
 #pragma unroll
-        for (int j = 0; j < 4; j++) acc[i][j] = 0.0;
+        for (int j = 0; j < 4; j++) acc[i][j] = S(0);
       for (int kk = 0; kk < k; kk += 16) {
         __syncthreads();
         for (int e = threadIdx.x; e < 1024; e += BLR_NT) {
           int r, cc;
           if (!ta) { r = e & 63; cc = e >> 6; } else { cc = e & 15; r = e >> 4; }
           int gr = tm + r, gk = kk + cc;
-          double v = 0.0;
-          if (gr < m && gk < k) v = ta ? ldg(A + gk + (long long)gr * lda) : ldg(A + gr + (long long)gk * lda);
+          S v = S(0);
+          if (gr < m && gk < k) v = (S)(ta ? ldg(A + gk + (long long)gr * lda) : ldg(A + gr + (long long)gk * lda));
           As[r + cc * 65] = v;
         }
         for (int e = threadIdx.x; e < 1024; e += BLR_NT) {
           int cc, nn;
           if (!tb) { cc = e & 15; nn = e >> 4; } else { nn = e & 63; cc = e >> 6; }
           int gk = kk + cc, gn = tn + nn;
-          double v = 0.0;
-          if (gn < n && gk < k) v = tb ? ldg(B + gn + (long long)gk * ldb) : ldg(B + gk + (long long)gn * ldb);
+          S v = S(0);
+          if (gn < n && gk < k) v = (S)(tb ? ldg(B + gn + (long long)gk * ldb) : ldg(B + gk + (long long)gn * ldb));
           Bs[cc * 64 + nn] = v;
         }
         __syncthreads();
         const int kmax = min(16, k - kk);
         for (int cc = 0; cc < kmax; cc++) {
-          double av[4], bv[4];
+          S av[4], bv[4];
 #pragma unroll
           for (int i = 0; i < 4; i++) av[i] = As[ty + 16 * i + cc * 65];
 #pragma unroll
@@ -492,10 +519,13 @@ __device__ void gemm(int m, int n, int k, double alpha, const double* A, long lo
         for (int j = 0; j < 4; j++) {
           int gr = tm + ty + 16 * i, gn = tn + tx + 16 * j;
           if (gr < m && gn < n) {
-            double* cp = C + gr + (long long)gn * ldc;
-            double v = alpha * acc[i][j];
-            if (beta != 0.0) v += beta * ldg(cp);
-            *cp = v;
+            GC* cp = C + gr + (long long)gn * ldc;
+            S v = alpha * acc[i][j];
+            if (beta != S(0)) {
+              *cp = (GC)v + (GC)beta * ldg(cp);
+            } else {
+              *cp = (GC)v;
+            }
           }
         }
       }
@@ -506,48 +536,63 @@ __device__ void gemm(int m, int n, int k, double alpha, const double* A, long lo
 }
 
 // ---------------------------------------------------------------------------
-// Blocked Householder QR of a global m x n matrix (m >= n) in place; T
-// blocks (one NB x NB per panel) at Tp + c0*NB (ld NB).
+// Blocked Householder QR of a global m x n matrix (m >= n) in place, all in
+// type S; T blocks (one NB x NB per panel) at Tp + c0*NB (ld NB).
 // ---------------------------------------------------------------------------
-__device__ void geqrf(double* A, long long lda, int m, int n, double* Tp, Ctx& c) {
+template <class S>
+__device__ void geqrf(S* A, long long lda, int m, int n, S* Tp, Ctx& c) {
+  S* pnl = as<S>(c.s.pnl);
+  S* tau = as<S>(c.s.tau);
+  S* Gm = as<S>(c.s.z);
+  S* Ts = as<S>(c.s.t);
   for (int c0 = 0; c0 < n; c0 += BLR_NB) {
     const int w = min(BLR_NB, n - c0), h = m - c0;
     if (h <= 0) break;
     const int ldp = h | 1;
     __syncthreads();
-    stage_in(c.s.pnl, ldp, colmajor(A + c0 + (long long)c0 * lda, (int)lda), h, w);
-    panel_qr(c.s.pnl, ldp, h, w, c.s.tau, c);
-    gram_panel(c.s.pnl, ldp, h, w, c.s.z, c);
-    t_recur(c.s.z, c.s.tau, w, c.s.t, c);
+    stage_in(pnl, ldp, colmajor(A + c0 + (long long)c0 * lda, lda), h, w);
+    panel_qr(pnl, ldp, h, w, tau, c);
+    gram_panel(pnl, ldp, h, w, Gm, c);
+    t_recur(Gm, tau, w, Ts, c);
     for (int e = threadIdx.x; e < BLR_NB * BLR_NB; e += BLR_NT) {
-      int a = e % BLR_NB, l = e / BLR_NB;
-      if (l < w) Tp[a + (long long)(c0 + l) * BLR_NB] = c.s.t[e];
+      int l = e / BLR_NB;
+      if (l < w) Tp[e + (long long)c0 * BLR_NB] = Ts[e];
     }
-    stage_out(colmajor(A + c0 + (long long)c0 * lda, (int)lda), c.s.pnl, ldp, h, w);
+    stage_out(colmajor(A + c0 + (long long)c0 * lda, lda), pnl, ldp, h, w);
     if (c0 + w < n)
-      apply_refl_panel(A + c0 + (long long)(c0 + w) * lda, lda, h, n - c0 - w, c.s.pnl, ldp, w,
-                       c.s.t, true, c);
+      apply_refl_panel(A + c0 + (long long)(c0 + w) * lda, lda, h, n - c0 - w, pnl, ldp, w, Ts, true, c);
     __syncthreads();
   }
 }
 
-// C (m x nc) <- Q^T C (trans) or Q C for Q from geqrf of an m x nref matrix.
-__device__ void apply_q(const double* Y, long long ldy, int m, int nref, const double* Tp, double* C,
-                        long long ldc, int nc, bool trans, Ctx& c) {
+// Stage panel c0 (rows c0..m-1, w columns) of stored reflectors Y (type GY)
+// and its T block (type GT) into shared memory as S; returns the ld.
+template <class S, class GY, class GT>
+__device__ int stage_panel(const GY* Y, long long ldy, int m, int c0, int w, const GT* Tp, Ctx& c) {
+  const int h = m - c0, ldp = h | 1;
+  __syncthreads();
+  stage_in(as<S>(c.s.pnl), ldp, colmajor(const_cast<GY*>(Y) + c0 + (long long)c0 * ldy, ldy), h, w);
+  S* Ts = as<S>(c.s.t);
+  for (int e = threadIdx.x; e < BLR_NB * BLR_NB; e += BLR_NT) {
+    int l = e / BLR_NB;
+    Ts[e] = (l < w) ? (S)ldg(Tp + e + (long long)c0 * BLR_NB) : S(0);
+  }
+  __syncthreads();
+  return ldp;
+}
+
+// C (m x nc) <- Q^T C (trans) or Q C for Q from geqrf of an m x nref matrix;
+// arithmetic in S.
+template <class S, class GY, class GT, class GC>
+__device__ void apply_q(const GY* Y, long long ldy, int m, int nref, const GT* Tp, GC* C, long long ldc, int nc,
+                        bool trans, Ctx& c) {
   const int npan = (nref + BLR_NB - 1) / BLR_NB;
   for (int pi = 0; pi < npan; pi++) {
     const int pp = trans ? pi : npan - 1 - pi;
     const int c0 = pp * BLR_NB, w = min(BLR_NB, nref - c0), h = m - c0;
     if (h <= 0) continue;
-    const int ldp = h | 1;
-    __syncthreads();
-    stage_in(c.s.pnl, ldp, colmajor(const_cast<double*>(Y) + c0 + (long long)c0 * ldy, (int)ldy), h, w);
-    for (int e = threadIdx.x; e < BLR_NB * BLR_NB; e += BLR_NT) {
-      int l = e / BLR_NB;
-      c.s.t[e] = (l < w) ? ldg(Tp + e + (long long)c0 * BLR_NB) : 0.0;
-    }
-    __syncthreads();
-    apply_refl_panel(C + c0, ldc, h, nc, c.s.pnl, ldp, w, c.s.t, trans, c);
+    const int ldp = stage_panel<S>(Y, ldy, m, c0, w, Tp, c);
+    apply_refl_panel(C + c0, ldc, h, nc, (const S*)as<S>(c.s.pnl), ldp, w, (const S*)as<S>(c.s.t), trans, c);
   }
 }
 
@@ -555,26 +600,27 @@ __device__ void apply_q(const double* Y, long long ldy, int m, int nref, const d
 // Column-pivoted Householder QR of a CTA-private m x n matrix (plain loads),
 // stopped at the smallest r whose trailing block has squared Frobenius norm
 // <= tol2, or when r reaches maxr (then *over = 1 if the tail is still
-// above tol2).  perm (length n, global or shared) receives the column order;
-// tau the reflector scalars.  Column norms are recomputed exactly each step.
+// above tol2).  perm (length n) receives the column order; tau the reflector
+// scalars.  Column norms are recomputed exactly each step.
 // ---------------------------------------------------------------------------
-__device__ int qrcp(double* A, long long lda, int m, int n, double tol2, int maxr, int* perm,
-                    double* tau, int* over, Ctx& c) {
+template <class S>
+__device__ int qrcp(S* A, long long lda, int m, int n, double tol2, int maxr, int* perm, S* tau, int* over,
+                    Ctx& c) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   double* cn = c.s.vec;   // column norms (n <= 512)
+  S* scal = as<S>(c.s.scal);
   for (int j = threadIdx.x; j < n; j += BLR_NT) perm[j] = j;
   if (threadIdx.x == 0) *over = 0;
   __syncthreads();
   int r = 0;
   const int kmax = min(m, n);
   while (true) {
-    // exact trailing column norms
     for (int col = r + warp; col < n; col += BLR_NWARP) {
-      double acc = 0.0;
-      const double* ap = A + (long long)col * lda;
+      S acc = S(0);
+      const S* ap = A + (long long)col * lda;
       for (int i = r + lane; i < m; i += 32) acc += ap[i] * ap[i];
       acc = warp_sum(acc);
-      if (lane == 0) cn[col] = acc;
+      if (lane == 0) cn[col] = (double)acc;
     }
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -597,7 +643,7 @@ __device__ int qrcp(double* A, long long lda, int m, int n, double tol2, int max
     c.fma += (double)(m - r) * (n - r);
     if (piv != r) {
       for (int i = threadIdx.x; i < m; i += BLR_NT) {
-        double t0 = A[i + (long long)r * lda];
+        S t0 = A[i + (long long)r * lda];
         A[i + (long long)r * lda] = A[i + (long long)piv * lda];
         A[i + (long long)piv * lda] = t0;
       }
@@ -606,31 +652,31 @@ __device__ int qrcp(double* A, long long lda, int m, int n, double tol2, int max
       }
     }
     __syncthreads();
-    double* ar = A + (long long)r * lda;
-    double part = 0.0;
+    S* ar = A + (long long)r * lda;
+    S part = S(0);
     for (int i = r + 1 + threadIdx.x; i < m; i += BLR_NT) part += ar[i] * ar[i];
-    double sig2 = block_sum(part, c.s.red);
+    S sig2 = block_sum(part, c.s.red);
     if (threadIdx.x == 0) {
-      double beta, tj, sc;
+      S beta, tj, sc;
       house(ar[r], sig2, beta, tj, sc);
-      flag_numeric(c, beta);
-      c.s.scal[0] = beta; c.s.scal[1] = tj; c.s.scal[2] = sc;
+      flag_numeric(c, (double)beta);
+      scal[0] = beta; scal[1] = tj; scal[2] = sc;
     }
     __syncthreads();
-    const double tj = c.s.scal[1], sc = c.s.scal[2];
+    const S tj = scal[1], sc = scal[2];
     for (int i = r + 1 + threadIdx.x; i < m; i += BLR_NT) ar[i] *= sc;
     __syncthreads();
     for (int col = r + 1 + warp; col < n; col += BLR_NWARP) {
-      double* ap = A + (long long)col * lda;
-      double acc = 0.0;
+      S* ap = A + (long long)col * lda;
+      S acc = S(0);
       for (int i = r + 1 + lane; i < m; i += 32) acc += ar[i] * ap[i];
       acc = warp_sum(acc);
-      double wl = (__shfl_sync(FULLMASK, ap[r], 0) + acc) * tj;
+      S wl = (__shfl_sync(FULLMASK, ap[r], 0) + acc) * tj;
       if (lane == 0) ap[r] -= wl;
       for (int i = r + 1 + lane; i < m; i += 32) ap[i] -= wl * ar[i];
     }
     __syncthreads();
-    if (threadIdx.x == 0) { ar[r] = c.s.scal[0]; tau[r] = tj; }
+    if (threadIdx.x == 0) { ar[r] = scal[0]; tau[r] = tj; }
     __syncthreads();
     c.fma += 2.0 * (m - r) * (n - r);
     r++;
@@ -641,21 +687,22 @@ __device__ int qrcp(double* A, long long lda, int m, int n, double tol2, int max
 
 // C (m x nc, CTA-private) <- Q C (trans = false) or Q^T C for the first nr
 // unblocked reflectors stored below the diagonal of A (from qrcp).
-__device__ void apply_q_unblocked(const double* A, long long lda, int m, int nr, const double* tau,
-                                  double* C, long long ldc, int nc, bool trans, Ctx& c) {
+template <class S>
+__device__ void apply_q_unblocked(const S* A, long long lda, int m, int nr, const S* tau, S* C, long long ldc,
+                                  int nc, bool trans, Ctx& c) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   for (int jj = 0; jj < nr; jj++) {
     const int j = trans ? jj : nr - 1 - jj;
-    const double* v = A + (long long)j * lda;
-    const double tj = tau[j];
+    const S* v = A + (long long)j * lda;
+    const S tj = tau[j];
     __syncthreads();
-    if (tj != 0.0) {
+    if (tj != S(0)) {
       for (int col = warp; col < nc; col += BLR_NWARP) {
-        double* cp = C + (long long)col * ldc;
-        double acc = 0.0;
+        S* cp = C + (long long)col * ldc;
+        S acc = S(0);
         for (int i = j + 1 + lane; i < m; i += 32) acc += v[i] * cp[i];
         acc = warp_sum(acc);
-        double wl = (__shfl_sync(FULLMASK, cp[j], 0) + acc) * tj;
+        S wl = (__shfl_sync(FULLMASK, cp[j], 0) + acc) * tj;
         if (lane == 0) cp[j] -= wl;
         for (int i = j + 1 + lane; i < m; i += 32) cp[i] -= wl * v[i];
       }
@@ -669,14 +716,14 @@ __device__ void apply_q_unblocked(const double* A, long long lda, int m, int nr,
 // One-sided (Hestenes) Jacobi on the columns of X (s x s, CTA-private, ld):
 // on exit the columns are mutually orthogonal, X = M V.  sig[j] = ||x_j||
 // and order[0..s) lists the columns by decreasing norm (ties: lower index).
-// Rotations are skipped once |x_p.x_q| <= tol sqrt(|x_p|^2 |x_q|^2).
+// Used by the fixed-rank (truncated SVD) compression.
 // ---------------------------------------------------------------------------
 __device__ void jacobi_svd(double* X, int ldx, int s, double* sig, int* order, Ctx& c) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const double tol = 1e-15;
-  double* nrm = sig;   // squared norms during the sweeps
-  const int np = (s + 1) & ~1;      // padded even count (index s is a dummy)
-  int* pos = order;                 // tournament positions (np <= 512)
+  double* nrm = sig;
+  const int np = (s + 1) & ~1;
+  int* pos = order;
   for (int j = threadIdx.x; j < s; j += BLR_NT) {
     double acc = 0.0;
     for (int i = 0; i < s; i++) acc += X[i + j * ldx] * X[i + j * ldx];
@@ -684,8 +731,7 @@ __device__ void jacobi_svd(double* X, int ldx, int s, double* sig, int* order, C
   }
   for (int j = threadIdx.x; j < np; j += BLR_NT) pos[j] = j;
   __syncthreads();
-  int sweeps = 0;
-  for (; sweeps < 40 && s > 1; sweeps++) {
+  for (int sweeps = 0; sweeps < 40 && s > 1; sweeps++) {
     if (threadIdx.x == 0) c.s.flag[2] = 0;
     __syncthreads();
     for (int round = 0; round < np - 1; round++) {
@@ -717,7 +763,6 @@ __device__ void jacobi_svd(double* X, int ldx, int s, double* sig, int* order, C
         }
       }
       __syncthreads();
-      // rotate tournament positions 1..np-1
       if (threadIdx.x == 0) {
         int last = pos[np - 1];
         for (int i = np - 1; i > 1; i--) pos[i] = pos[i - 1];
@@ -726,7 +771,6 @@ __device__ void jacobi_svd(double* X, int ldx, int s, double* sig, int* order, C
       __syncthreads();
     }
     c.fma += 2.5 * (double)s * s * s;
-    // refresh the squared norms exactly
     for (int j = threadIdx.x; j < s; j += BLR_NT) {
       double acc = 0.0;
       for (int i = 0; i < s; i++) acc += X[i + j * ldx] * X[i + j * ldx];
@@ -736,7 +780,6 @@ __device__ void jacobi_svd(double* X, int ldx, int s, double* sig, int* order, C
     if (c.s.flag[2] == 0) break;
     __syncthreads();
   }
-  // singular values and descending order
   for (int j = threadIdx.x; j < s; j += BLR_NT) sig[j] = sqrt(nrm[j]);
   __syncthreads();
   for (int j = threadIdx.x; j < s; j += BLR_NT) {
@@ -747,56 +790,36 @@ __device__ void jacobi_svd(double* X, int ldx, int s, double* sig, int* order, C
   __syncthreads();
 }
 
-// Smallest r with sum_{l>=r} sig_l^2 <= eps^2 sum sig_l^2 (sig in the given
-// descending order).  Thread 0 computes; all threads return it.
-__device__ int trunc_rank(const double* sig, const int* order, int s, double eps, Ctx& c) {
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double tot = 0.0;
-    for (int l = 0; l < s; l++) tot += sig[order[l]] * sig[order[l]];
-    int r = s;
-    if (tot == 0.0) r = 0;
-    else {
-      const double thr = (eps * sqrt(tot)) * (eps * sqrt(tot));
-      double tail = 0.0;
-      r = s;
-      for (int l = s - 1; l >= 0; l--) {   // tail[l] = sum_{>= l}
-        double nt = tail + sig[order[l]] * sig[order[l]];
-        if (nt <= thr) { tail = nt; r = l; } else break;
-      }
-    }
-    c.s.flag[3] = r;
-  }
-  __syncthreads();
-  return c.s.flag[3];
-}
-
-// Stage panel c0 of a reduced reflector: Yr(:, c0:c0+w) into c.s.pnl and
-// its T block into c.s.t.  Returns the shared-memory leading dimension.
-__device__ int stage_reflector_panel(View Yr, int ry, int c0, int w, const double* Tik, Ctx& c) {
+// ---------------------------------------------------------------------------
+// Reduced reflectors of a TSQRT: Q = I - [I; Yr] T [I; Yr]^T with Yr (ry x b,
+// view of type GY) and T blocks (32 x b, type GT).
+// ---------------------------------------------------------------------------
+template <class S, class GY, class GT>
+__device__ int stage_reflector_panel(View<GY> Yr, int ry, int c0, int w, const GT* Tik, Ctx& c) {
   const int ldy = ry | 1;
   __syncthreads();
-  View src{Yr.p + c0 * Yr.sc, Yr.sr, Yr.sc};
-  stage_in(c.s.pnl, ldy, src, ry, w);
+  stage_in(as<S>(c.s.pnl), ldy, Yr.shifted(0, c0), ry, w);
+  S* Ts = as<S>(c.s.t);
   for (int e = threadIdx.x; e < BLR_NB * BLR_NB; e += BLR_NT) {
     int l = e / BLR_NB;
-    c.s.t[e] = (l < w) ? ldg(Tik + e + (size_t)c0 * BLR_NB) : 0.0;
+    Ts[e] = (l < w) ? (S)ldg(Tik + e + (size_t)c0 * BLR_NB) : S(0);
   }
   __syncthreads();
   return ldy;
 }
 
 // [Ctop (b x nc, ld ldt); Cbot (ry x nc)] <- Q^T (trans) or Q times it, for
-// the reduced reflector Q = I - [I; Yr] T [I; Yr]^T of a TSQRT (b reflectors
-// in blocks of 32).
-__device__ void apply_ts_reflector(View Yr, int ry, int b, const double* Tik, double* Ctop,
-                                   long long ldt, View Cbot, int nc, bool trans, Ctx& c) {
+// the b reflectors of a TSQRT in blocks of 32; arithmetic in S.
+template <class S, class GY, class GT, class GC, class GB>
+__device__ void apply_ts_reflector(View<GY> Yr, int ry, int b, const GT* Tik, GC* Ctop, long long ldt,
+                                   View<GB> Cbot, int nc, bool trans, Ctx& c) {
   const int npan = b / BLR_NB;
   for (int pi = 0; pi < npan; pi++) {
     const int pp = trans ? pi : npan - 1 - pi;
     const int c0 = pp * BLR_NB;
-    const int ldy = stage_reflector_panel(Yr, ry, c0, BLR_NB, Tik, c);
-    apply_refl_ts(Ctop + c0, ldt, Cbot, ry, nc, c.s.pnl, ldy, BLR_NB, c.s.t, trans, c);
+    const int ldy = stage_reflector_panel<S>(Yr, ry, c0, BLR_NB, Tik, c);
+    apply_refl_ts(Ctop + c0, ldt, Cbot, ry, nc, (const S*)as<S>(c.s.pnl), ldy, BLR_NB, (const S*)as<S>(c.s.t),
+                  trans, c);
   }
 }
 

@@ -50,7 +50,7 @@ __device__ __forceinline__ int ld_rank(const int* p) { return __ldcg(p); }
 
 // ---------------------------------------------------------------------------
 // TSQRT panel: Householder on [Rp (w x w upper, ld NB); Bp (ry x w, ld ldb)],
-// reflector j = [e_j; y_j] (Section 3.4.3).
+// reflector j = [e_j; y_j] (Section 3.4.3).  Always FP64.
 // ---------------------------------------------------------------------------
 __device__ void ts_panel_qr(double* Rp, double* Bp, int ldb, int ry, int w, double* tau, Ctx& c) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -103,11 +103,13 @@ __device__ void ts_panel_qr(double* Rp, double* Bp, int ldb, int ry, int w, doub
 // and V_C = Q_H [P R_M(0:r,:)^T; 0].  (Algorithm 6 truncates the core's SVD;
 // the pivoted QR reaches the same error bound in O(s^2 r) work instead of
 // O(s^3) per Jacobi sweep, with a rank that can exceed the optimal one by a
-// few.)  Uf is overwritten.  A result whose rank would exceed dense_rank is
-// written as the dense product Uf0 H0^T.
+// few.)  Uf is overwritten.  The result goes to dest in tile layout (U at 0,
+// V at b*cap); one whose rank would exceed dense_rank is written dense as
+// the product Uf0 H0^T.  Arithmetic in S.
 // ---------------------------------------------------------------------------
-__device__ void recompress_side(TaskEnv& env, double* Uf, int ldu, const double* H, const double* TH,
-                                const double* H0, int s, double* dest, int* dest_rank, Ctx& c) {
+template <class S>
+__device__ void recompress_side(TaskEnv& env, S* Uf, int ldu, const S* H, const S* TH, const S* H0, int s,
+                                S* dest, int* dest_rank, Ctx& c) {
   const SchedParams& P = *env.P;
   const int b = P.b;
   const size_t mark = env.used;
@@ -116,34 +118,32 @@ __device__ void recompress_side(TaskEnv& env, double* Uf, int ldu, const double*
     __syncthreads();
     return;
   }
-  double* U0 = env.alloc((size_t)b * s);
+  S* U0 = (S*)env.alloc(((size_t)b * s * sizeof(S) + 7) / 8);
   copy_mat(U0, b, Uf, ldu, b, s);
-  double* TU = env.alloc((size_t)BLR_NB * s);
+  S* TU = (S*)env.alloc(((size_t)BLR_NB * s * sizeof(S) + 7) / 8);
   __syncthreads();
   geqrf(Uf, ldu, b, s, TU, c);
-  // M = R_U R_H^T  (upper triangular factors)
-  double* RU = env.alloc((size_t)s * s);
-  double* RH = env.alloc((size_t)s * s);
+  S* RU = (S*)env.alloc(((size_t)s * s * sizeof(S) + 7) / 8);
+  S* RH = (S*)env.alloc(((size_t)s * s * sizeof(S) + 7) / 8);
   for (int e = threadIdx.x; e < s * s; e += BLR_NT) {
     int a = e % s, l = e / s;
-    RU[e] = (a <= l) ? ldg(Uf + a + (size_t)l * ldu) : 0.0;
-    RH[e] = (a <= l) ? ldg(H + a + (size_t)l * b) : 0.0;
+    RU[e] = (a <= l) ? ldg(Uf + a + (size_t)l * ldu) : S(0);
+    RH[e] = (a <= l) ? ldg(H + a + (size_t)l * b) : S(0);
   }
   __syncthreads();
-  double* M = env.alloc((size_t)s * s);
-  gemm(s, s, s, 1.0, RU, s, false, RH, s, true, 0.0, M, s, c);
+  S* M = (S*)env.alloc(((size_t)s * s * sizeof(S) + 7) / 8);
+  gemm(s, s, s, S(1), RU, s, false, RH, s, true, S(0), M, s, c);
   double part = 0.0;
-  for (int e = threadIdx.x; e < s * s; e += BLR_NT) part += M[e] * M[e];
+  for (int e = threadIdx.x; e < s * s; e += BLR_NT) part += (double)M[e] * (double)M[e];
   const double nrm2 = block_sum(part, c.s.red);
   const double tol2 = P.rec_tol * P.rec_tol * nrm2;
-  double* tauM = env.alloc((size_t)s);
+  S* tauM = (S*)env.alloc(((size_t)s * sizeof(S) + 7) / 8);
   int* perm = c.s.ivec;
   const int r = qrcp(M, s, s, s, tol2, P.dense_rank, perm, tauM, c.s.flag + 2, c);
   const int over = c.s.flag[2];
   __syncthreads();
   if (over) {
-    // dense fallback: the exact sum
-    gemm(b, b, s, 1.0, U0, b, false, H0, b, true, 0.0, dest, b, c);
+    gemm(b, b, s, S(1), U0, b, false, H0, b, true, S(0), dest, b, c);
     __syncthreads();
     if (threadIdx.x == 0) *dest_rank = -1;
     __syncthreads();
@@ -151,21 +151,20 @@ __device__ void recompress_side(TaskEnv& env, double* Uf, int ldu, const double*
     return;
   }
   if (r > 0) {
-    double* CU = env.alloc((size_t)b * r);
-    double* CV = env.alloc((size_t)b * r);
+    S* CU = (S*)env.alloc(((size_t)b * r * sizeof(S) + 7) / 8);
+    S* CV = (S*)env.alloc(((size_t)b * r * sizeof(S) + 7) / 8);
     zero_mat(CU, b, b, r);
     zero_mat(CV, b, b, r);
     __syncthreads();
-    for (int l = threadIdx.x; l < r; l += BLR_NT) CU[l + (size_t)l * b] = 1.0;
-    // V part: P R_M(0:r,:)^T
+    for (int l = threadIdx.x; l < r; l += BLR_NT) CU[l + (size_t)l * b] = S(1);
     for (int e = threadIdx.x; e < s * r; e += BLR_NT) {
       int cc = e % s, l = e / s;
-      CV[perm[cc] + (size_t)l * b] = (cc >= l) ? M[l + (size_t)cc * s] : 0.0;
+      CV[perm[cc] + (size_t)l * b] = (cc >= l) ? M[l + (size_t)cc * s] : S(0);
     }
     __syncthreads();
-    apply_q_unblocked(M, s, s, r, tauM, CU, b, r, false, c);   // Q_M [I_r; 0] in the top s rows
-    apply_q(Uf, ldu, b, s, TU, CU, b, r, false, c);
-    apply_q(H, b, b, s, TH, CV, b, r, false, c);
+    apply_q_unblocked(M, s, s, r, tauM, CU, b, r, false, c);
+    apply_q<S>(Uf, ldu, b, s, TU, CU, b, r, false, c);
+    apply_q<S>(H, b, b, s, TH, CV, b, r, false, c);
     copy_mat(dest, b, CU, b, b, r);
     copy_mat(dest + (size_t)b * P.cap, b, CV, b, b, r);
   }
@@ -176,28 +175,56 @@ __device__ void recompress_side(TaskEnv& env, double* Uf, int ldu, const double*
 }
 
 // ---------------------------------------------------------------------------
-// Task bodies
+// Task bodies.  S is the arithmetic of the trailing compact-WY updates and of
+// the recompressions: double on the FP64 path, float on the mixed path.
+// Panel factorizations (Householder norms, tau, vectors, T) are FP64 on both.
 // ---------------------------------------------------------------------------
 
 // GEQRT(k): Householder QR of the dense diagonal tile (Section 3.4.1).
+template <class S>
 __device__ void task_geqrt(TaskEnv& env, int k, Ctx& c) {
   const SchedParams& P = *env.P;
+  const int b = P.b;
   double* A = tile_ptr(P, k, k);
-  geqrf(A, P.b, P.b, P.b, t_ptr(P, k, k), c);
+  double* Tp = t_ptr(P, k, k);
+  if (std::is_same<S, double>::value) {
+    geqrf(A, b, b, b, Tp, c);
+    return;
+  }
+  double* pnl = c.s.pnl;
+  for (int c0 = 0; c0 < b; c0 += BLR_NB) {
+    const int w = BLR_NB, h = b - c0, ldp = h | 1;
+    __syncthreads();
+    stage_in(pnl, ldp, colmajor(A + c0 + (size_t)c0 * b, b), h, w);
+    panel_qr(pnl, ldp, h, w, c.s.tau, c);
+    gram_panel(pnl, ldp, h, w, c.s.z, c);
+    t_recur(c.s.z, c.s.tau, w, c.s.t, c);
+    for (int e = threadIdx.x; e < BLR_NB * BLR_NB; e += BLR_NT) Tp[e + (size_t)c0 * BLR_NB] = c.s.t[e];
+    stage_out(colmajor(A + c0 + (size_t)c0 * b, b), pnl, ldp, h, w);
+    __syncthreads();
+    if (c0 + w < b) {
+      const int ldq = stage_panel<S>(A, b, b, c0, w, Tp, c);
+      apply_refl_panel(A + c0 + (size_t)(c0 + w) * b, b, h, b - c0 - w, (const S*)as<S>(c.s.pnl), ldq, w,
+                       (const S*)as<S>(c.s.t), true, c);
+    }
+  }
 }
 
 // LARFB(k,j): R_kj = Q_kk^T A_kj (Section 3.4.2): U <- Q^T U, or the dense tile.
+template <class S>
 __device__ void task_larfb(TaskEnv& env, int k, int j, Ctx& c) {
   const SchedParams& P = *env.P;
   const int b = P.b;
   const int r = ld_rank(rank_ptr(P, k, j));
   double* C = tile_ptr(P, k, j);
   const int nc = (r < 0) ? b : r;
-  if (nc > 0) apply_q(tile_ptr(P, k, k), b, b, b, t_ptr(P, k, k), C, b, nc, true, c);
+  if (nc > 0) apply_q<S>(tile_ptr(P, k, k), b, b, b, t_ptr(P, k, k), C, b, nc, true, c);
 }
 
 // TSQRT(i,k): QR([R_kk; A^V_ik]) with A^V = V^T (low-rank) or the dense tile
-// (Section 3.4.3, Eqs. 19-21); Y_ik overwrites A^V in place.
+// (Section 3.4.3, Eqs. 19-21); Y_ik overwrites A^V in place.  The panel
+// factorization is FP64; the update of the trailing columns runs in S.
+template <class S>
 __device__ void task_tsqrt(TaskEnv& env, int i, int k, Ctx& c) {
   const SchedParams& P = *env.P;
   const int b = P.b;
@@ -206,7 +233,7 @@ __device__ void task_tsqrt(TaskEnv& env, int i, int k, Ctx& c) {
   double* Tk = t_ptr(P, i, k);
   double* B = tile_ptr(P, i, k);
   const int ry = (r < 0) ? b : r;
-  View Bv = (r < 0) ? colmajor(B, b) : rowmajor(B + (size_t)b * P.cap, b);
+  View<double> Bv = (r < 0) ? colmajor(B, b) : rowmajor(B + (size_t)b * P.cap, b);
   if (ry == 0) {
     for (int e = threadIdx.x; e < BLR_NB * b; e += BLR_NT) Tk[e] = 0.0;
     __syncthreads();
@@ -220,7 +247,7 @@ __device__ void task_tsqrt(TaskEnv& env, int i, int k, Ctx& c) {
       int a = e % w, l = e / w;
       c.s.rp[a + l * BLR_NB] = (a <= l) ? ldg(R + (c0 + a) + (size_t)(c0 + l) * b) : 0.0;
     }
-    View Bp{Bv.p + c0 * Bv.sc, Bv.sr, Bv.sc};
+    View<double> Bp = Bv.shifted(0, c0);
     stage_in(c.s.pnl, ldb, Bp, ry, w);
     ts_panel_qr(c.s.rp, c.s.pnl, ldb, ry, w, c.s.tau, c);
     gram_dense(c.s.pnl, ldb, ry, w, c.s.z, c);
@@ -231,10 +258,16 @@ __device__ void task_tsqrt(TaskEnv& env, int i, int k, Ctx& c) {
       if (a <= l) R[(c0 + a) + (size_t)(c0 + l) * b] = c.s.rp[a + l * BLR_NB];
     }
     stage_out(Bp, c.s.pnl, ldb, ry, w);
+    __syncthreads();
     if (c0 + w < b) {
-      View Cb{Bv.p + (c0 + w) * Bv.sc, Bv.sr, Bv.sc};
-      apply_refl_ts(R + c0 + (size_t)(c0 + w) * b, b, Cb, ry, b - c0 - w, c.s.pnl, ldb, w, c.s.t,
-                    true, c);
+      View<double> Cb = Bv.shifted(0, c0 + w);
+      if (std::is_same<S, double>::value) {
+        apply_refl_ts(R + c0 + (size_t)(c0 + w) * b, b, Cb, ry, b - c0 - w, c.s.pnl, ldb, w, c.s.t, true, c);
+      } else {
+        const int ldy = stage_reflector_panel<S>(Bv, ry, c0, w, Tk, c);
+        apply_refl_ts(R + c0 + (size_t)(c0 + w) * b, b, Cb, ry, b - c0 - w, (const S*)as<S>(c.s.pnl), ldy, w,
+                      (const S*)as<S>(c.s.t), true, c);
+      }
     }
     __syncthreads();
   }
@@ -247,66 +280,59 @@ __device__ void task_tsqrt(TaskEnv& env, int i, int k, Ctx& c) {
 // R_kj and A_ij are low-rank the pair is kept factored, [R; P] = G H^T, the
 // reflector is applied to G, and both results are recompressed by the
 // rounded addition of Algorithm 6 (sharing the QR of H).
-__device__ void task_tpmqrt(TaskEnv& env, int i, int j, int k, Ctx& c) {
+//
+// Operands are tile-layout buffers of type S (U at 0, V at b*cap, or dense
+// b x b); rY/rR/rA are their ranks (-1 dense); new ranks go to *nR, *nA.
+template <class S>
+__device__ void tpmqrt_core(TaskEnv& env, S* Yt, int rY, const S* Tik, S* Rt, int rR, S* At, int rA, int* nR,
+                            int* nA, Ctx& c) {
   const SchedParams& P = *env.P;
   const int b = P.b, cap = P.cap;
-  const int rY = ld_rank(rank_ptr(P, i, k));
-  const int rR = ld_rank(rank_ptr(P, k, j));
-  const int rA = ld_rank(rank_ptr(P, i, j));
+  auto alloc = [&](size_t n) { return (S*)env.alloc((n * sizeof(S) + 7) / 8); };
   const bool ylr = rY >= 0;
   if (ylr && rY == 0) return;           // the reflector is the identity
   const int ry = ylr ? rY : b;
-  double* Yt = tile_ptr(P, i, k);
-  double* Uy = Yt;                      // U_ik when low-rank
-  View Yr = ylr ? rowmajor(Yt + (size_t)b * cap, b) : colmajor(Yt, b);
-  const double* Tik = t_ptr(P, i, k);
-  double* Rt = tile_ptr(P, k, j);
-  double* At = tile_ptr(P, i, j);
-  int* rankR = rank_ptr(P, k, j);
-  int* rankA = rank_ptr(P, i, j);
+  S* Uy = Yt;
+  View<S> Yr = ylr ? rowmajor(Yt + (size_t)b * cap, b) : colmajor(Yt, b);
 
   if (rR >= 0 && (rA >= 0 || ylr)) {
     // ---------------- factored paths -----------------
-    const bool adense = rA < 0;         // F2: A dense, Y low-rank
+    const bool adense = rA < 0;         // A dense, Y low-rank
     const int s2 = adense ? ry : rA;    // columns of the P part
     const int s = rR + s2;
     if (s == 0) return;
     const int ldG = b + ry;
-    double* G = env.alloc((size_t)ldG * s);
-    double* H = env.alloc((size_t)b * s);
-    double* H0 = env.alloc((size_t)b * s);
-    double* PU0 = env.alloc((size_t)ry * s2);
+    S* G = alloc((size_t)ldG * s);
+    S* H = alloc((size_t)b * s);
+    S* H0 = alloc((size_t)b * s);
+    S* PU0 = alloc((size_t)ry * s2);
     zero_mat(G, ldG, ldG, s);
     __syncthreads();
     copy_mat(G, ldG, Rt, b, b, rR);                              // U_R
     copy_mat(H, b, Rt + (size_t)b * cap, b, b, rR);              // V_R
     if (!adense) {
-      // P = (U_ik^T U_A) V_A^T: G_bot(:, rR:) = U_ik^T U_A, H(:, rR:) = V_A
-      if (ylr) gemm(ry, rA, b, 1.0, Uy, b, true, At, b, false, 0.0, G + b + (size_t)rR * ldG, ldG, c);
+      if (ylr) gemm(ry, rA, b, S(1), Uy, b, true, At, b, false, S(0), G + b + (size_t)rR * ldG, ldG, c);
       else copy_mat(G + b + (size_t)rR * ldG, ldG, At, b, b, rA);
       copy_mat(H + (size_t)rR * b, b, At + (size_t)b * cap, b, b, rA);
     } else {
-      // P = U_ik^T A (ry x b): G_bot(:, rR:) = I, H(:, rR:) = P^T
-      gemm(b, ry, b, 1.0, At, b, true, Uy, b, false, 0.0, H + (size_t)rR * b, b, c);
+      gemm(b, ry, b, S(1), At, b, true, Uy, b, false, S(0), H + (size_t)rR * b, b, c);
       __syncthreads();
-      for (int e = threadIdx.x; e < ry; e += BLR_NT) G[b + e + (size_t)(rR + e) * ldG] = 1.0;
+      for (int e = threadIdx.x; e < ry; e += BLR_NT) G[b + e + (size_t)(rR + e) * ldG] = S(1);
     }
     __syncthreads();
     copy_mat(PU0, ry, G + b + (size_t)rR * ldG, ldG, ry, s2);
     copy_mat(H0, b, H, b, b, s);
     __syncthreads();
-    // apply the reduced reflector to G
-    apply_ts_reflector(Yr, ry, b, Tik, G, ldG, colmajor(G + b, ldG), s, true, c);
-    // Delta G = G_bot' - G_bot
+    apply_ts_reflector<S>(Yr, ry, b, Tik, G, ldG, colmajor(G + b, ldG), s, true, c);
     for (int e = threadIdx.x; e < ry * s2; e += BLR_NT) {
       int a = e % ry, l = e / ry;
       G[b + a + (size_t)(rR + l) * ldG] -= PU0[e];
     }
     __syncthreads();
+    S* TH = alloc((size_t)BLR_NB * s);
     if (!adense) {
-      // A_new = Uf_A H^T with Uf_A = U_ik dG + [0, U_A] (or dG + [0, U_A] for dense Y)
-      double* UfA = env.alloc((size_t)b * s);
-      if (ylr) gemm(b, s, ry, 1.0, Uy, b, false, G + b, ldG, false, 0.0, UfA, b, c);
+      S* UfA = alloc((size_t)b * s);
+      if (ylr) gemm(b, s, ry, S(1), Uy, b, false, G + b, ldG, false, S(0), UfA, b, c);
       else copy_mat(UfA, b, G + b, ldG, b, s);
       __syncthreads();
       for (int e = threadIdx.x; e < b * rA; e += BLR_NT) {
@@ -314,51 +340,47 @@ __device__ void task_tpmqrt(TaskEnv& env, int i, int j, int k, Ctx& c) {
         UfA[a + (size_t)(rR + l) * b] += ldg(At + a + (size_t)l * b);
       }
       __syncthreads();
-      double* TH = env.alloc((size_t)BLR_NB * s);
       geqrf(H, b, b, s, TH, c);
-      recompress_side(env, G, ldG, H, TH, H0, s, Rt, rankR, c);
-      recompress_side(env, UfA, b, H, TH, H0, s, At, rankA, c);
+      recompress_side(env, G, ldG, H, TH, H0, s, Rt, nR, c);
+      recompress_side(env, UfA, b, H, TH, H0, s, At, nA, c);
     } else {
-      // A += (U_ik dG) H0^T (dense update), then recompress R
-      double* M1 = env.alloc((size_t)b * s);
-      gemm(b, s, ry, 1.0, Uy, b, false, G + b, ldG, false, 0.0, M1, b, c);
-      gemm(b, b, s, 1.0, M1, b, false, H0, b, true, 1.0, At, b, c);
-      double* TH = env.alloc((size_t)BLR_NB * s);
+      S* M1 = alloc((size_t)b * s);
+      gemm(b, s, ry, S(1), Uy, b, false, G + b, ldG, false, S(0), M1, b, c);
+      gemm(b, b, s, S(1), M1, b, false, H0, b, true, S(1), At, b, c);
       geqrf(H, b, b, s, TH, c);
-      recompress_side(env, G, ldG, H, TH, H0, s, Rt, rankR, c);
+      recompress_side(env, G, ldG, H, TH, H0, s, Rt, nR, c);
     }
     return;
   }
 
   // ---------------- dense path: R_kj dense (or becomes dense) -----------------
-  double* Rd;
+  S* Rd;
   bool r_scratch = false;
   if (rR < 0) {
     Rd = Rt;
   } else {
-    // R low-rank with dense Y and dense A: R + Y~^T A is dense (OP1)
-    Rd = env.alloc((size_t)b * b);
-    if (rR > 0) gemm(b, b, rR, 1.0, Rt, b, false, Rt + (size_t)b * cap, b, true, 0.0, Rd, b, c);
+    Rd = alloc((size_t)b * b);
+    if (rR > 0) gemm(b, b, rR, S(1), Rt, b, false, Rt + (size_t)b * cap, b, true, S(0), Rd, b, c);
     else zero_mat(Rd, b, b, b);
     r_scratch = true;
   }
-  double* Pm;
+  S* Pm;
   int ldp;
-  double* P0 = nullptr;
+  S* P0 = nullptr;
   bool a_inplace = false;
   if (ylr) {
     ldp = ry;
-    Pm = env.alloc((size_t)ry * b);
+    Pm = alloc((size_t)ry * b);
     if (rA < 0) {
-      gemm(ry, b, b, 1.0, Uy, b, true, At, b, false, 0.0, Pm, ry, c);
+      gemm(ry, b, b, S(1), Uy, b, true, At, b, false, S(0), Pm, ry, c);
     } else if (rA == 0) {
       zero_mat(Pm, ry, ry, b);
     } else {
-      double* PU = env.alloc((size_t)ry * rA);
-      gemm(ry, rA, b, 1.0, Uy, b, true, At, b, false, 0.0, PU, ry, c);
-      gemm(ry, b, rA, 1.0, PU, ry, false, At + (size_t)b * cap, b, true, 0.0, Pm, ry, c);
+      S* PU = alloc((size_t)ry * rA);
+      gemm(ry, rA, b, S(1), Uy, b, true, At, b, false, S(0), PU, ry, c);
+      gemm(ry, b, rA, S(1), PU, ry, false, At + (size_t)b * cap, b, true, S(0), Pm, ry, c);
     }
-    P0 = env.alloc((size_t)ry * b);
+    P0 = alloc((size_t)ry * b);
     __syncthreads();
     copy_mat(P0, ry, Pm, ry, ry, b);
   } else {
@@ -367,54 +389,105 @@ __device__ void task_tpmqrt(TaskEnv& env, int i, int j, int k, Ctx& c) {
       Pm = At;
       a_inplace = true;
     } else {
-      Pm = env.alloc((size_t)b * b);
-      if (rA > 0) gemm(b, b, rA, 1.0, At, b, false, At + (size_t)b * cap, b, true, 0.0, Pm, b, c);
+      Pm = alloc((size_t)b * b);
+      if (rA > 0) gemm(b, b, rA, S(1), At, b, false, At + (size_t)b * cap, b, true, S(0), Pm, b, c);
       else zero_mat(Pm, b, b, b);
     }
   }
   __syncthreads();
-  apply_ts_reflector(Yr, ry, b, Tik, Rd, b, colmajor(Pm, ldp), b, true, c);
+  apply_ts_reflector<S>(Yr, ry, b, Tik, Rd, b, colmajor(Pm, ldp), b, true, c);
   if (r_scratch) {
     copy_mat(Rt, b, Rd, b, b, b);
     __syncthreads();
-    if (threadIdx.x == 0) *rankR = -1;
+    if (threadIdx.x == 0) *nR = -1;
   }
   __syncthreads();
   if (!ylr) {
     if (!a_inplace) {
       copy_mat(At, b, Pm, b, b, b);
       __syncthreads();
-      if (threadIdx.x == 0) *rankA = -1;
+      if (threadIdx.x == 0) *nA = -1;
     }
     __syncthreads();
     return;
   }
-  // dP = P' - P
   for (int e = threadIdx.x; e < ry * b; e += BLR_NT) Pm[e] -= P0[e];
   __syncthreads();
   if (rA < 0) {
-    gemm(b, b, ry, 1.0, Uy, b, false, Pm, ry, false, 1.0, At, b, c);
+    gemm(b, b, ry, S(1), Uy, b, false, Pm, ry, false, S(1), At, b, c);
     return;
   }
-  // A_new = [U_A, U_ik] [V_A, dP^T]^T, recompressed
   const int s = rA + ry;
-  double* Uf = env.alloc((size_t)b * s);
-  double* H = env.alloc((size_t)b * s);
-  double* H0 = env.alloc((size_t)b * s);
+  S* Uf = alloc((size_t)b * s);
+  S* H = alloc((size_t)b * s);
+  S* H0 = alloc((size_t)b * s);
   copy_mat(Uf, b, At, b, b, rA);
   copy_mat(Uf + (size_t)rA * b, b, Uy, b, b, ry);
   copy_mat(H, b, At + (size_t)b * cap, b, b, rA);
   __syncthreads();
   for (int e = threadIdx.x; e < b * ry; e += BLR_NT) {
-    int a = e % b, l = e / b;      // H(:, rA + l) = dP(l, :)^T
+    int a = e % b, l = e / b;
     H[a + (size_t)(rA + l) * b] = Pm[l + (size_t)a * ldp];
   }
   __syncthreads();
   copy_mat(H0, b, H, b, b, s);
-  double* TH = env.alloc((size_t)BLR_NB * s);
+  S* TH = alloc((size_t)BLR_NB * s);
   __syncthreads();
   geqrf(H, b, b, s, TH, c);
-  recompress_side(env, Uf, b, H, TH, H0, s, At, rankA, c);
+  recompress_side(env, Uf, b, H, TH, H0, s, At, nA, c);
+}
+
+// Copies the live part of a tile (rank r: U and V columns; -1: dense) between
+// storage types.
+template <class D, class Src>
+__device__ void copy_tile(D* dst, const Src* src, int r, int b, int cap) {
+  if (r < 0) {
+    copy_mat(dst, b, src, b, b, b);
+  } else if (r > 0) {
+    copy_mat(dst, b, src, b, b, r);
+    copy_mat(dst + (size_t)b * cap, b, src + (size_t)b * cap, b, b, r);
+  }
+}
+
+template <class S>
+__device__ void task_tpmqrt(TaskEnv& env, int i, int j, int k, Ctx& c) {
+  const SchedParams& P = *env.P;
+  const int b = P.b, cap = P.cap;
+  const int rY = ld_rank(rank_ptr(P, i, k));
+  const int rR = ld_rank(rank_ptr(P, k, j));
+  const int rA = ld_rank(rank_ptr(P, i, j));
+  double* Yt = tile_ptr(P, i, k);
+  double* Rt = tile_ptr(P, k, j);
+  double* At = tile_ptr(P, i, j);
+  const double* Tik = t_ptr(P, i, k);
+  if (std::is_same<S, double>::value) {
+    tpmqrt_core<double>(env, Yt, rY, Tik, Rt, rR, At, rA, rank_ptr(P, k, j), rank_ptr(P, i, j), c);
+    return;
+  }
+  if (rY == 0) return;
+  // mixed: FP32 copies of the operands, FP32 arithmetic, results back to FP64
+  float* Yf = (float*)env.alloc((size_t)b * b / 2);
+  float* Tf = (float*)env.alloc((size_t)BLR_NB * b / 2);
+  float* Rf = (float*)env.alloc((size_t)b * b / 2);
+  float* Af = (float*)env.alloc((size_t)b * b / 2);
+  copy_tile(Yf, Yt, rY, b, cap);
+  copy_mat(Tf, BLR_NB, Tik, BLR_NB, BLR_NB, b);
+  copy_tile(Rf, Rt, rR, b, cap);
+  copy_tile(Af, At, rA, b, cap);
+  __shared__ int newr[2];
+  if (threadIdx.x == 0) { newr[0] = rR; newr[1] = rA; }
+  __syncthreads();
+  tpmqrt_core<float>(env, Yf, rY, Tf, Rf, rR, Af, rA, &newr[0], &newr[1], c);
+  __syncthreads();
+  const int r1 = newr[0], r2 = newr[1];
+  copy_tile(Rt, Rf, r1, b, cap);
+  copy_tile(At, Af, r2, b, cap);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    *rank_ptr(P, k, j) = r1;
+    *rank_ptr(P, i, j) = r2;
+  }
+  __syncthreads();
 }
 
 // ---------------------------------------------------------------------------
@@ -493,11 +566,12 @@ __global__ void __launch_bounds__(BLR_NT, 1) k_factor(SchedParams P) {
     c.fma = 0.0;
     env.used = 0;
     env.overflow = false;
+    const bool mixed = P.precision == BLR_PREC_MIXED;
     switch (type) {
-      case TASK_GEQRT: task_geqrt(env, k, c); break;
-      case TASK_LARFB: task_larfb(env, k, j, c); break;
-      case TASK_TSQRT: task_tsqrt(env, i, k, c); break;
-      case TASK_TPMQRT: task_tpmqrt(env, i, j, k, c); break;
+      case TASK_GEQRT: mixed ? task_geqrt<float>(env, k, c) : task_geqrt<double>(env, k, c); break;
+      case TASK_LARFB: mixed ? task_larfb<float>(env, k, j, c) : task_larfb<double>(env, k, j, c); break;
+      case TASK_TSQRT: mixed ? task_tsqrt<float>(env, i, k, c) : task_tsqrt<double>(env, i, k, c); break;
+      case TASK_TPMQRT: mixed ? task_tpmqrt<float>(env, i, j, k, c) : task_tpmqrt<double>(env, i, j, k, c); break;
       default:
         if (threadIdx.x == 0) atomicOr(P.status, ST_BADTASK);
         break;

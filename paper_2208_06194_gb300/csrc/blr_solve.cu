@@ -38,7 +38,7 @@ __device__ void apply_ts_tile(const FactorView& F, int i, int k, double* Ck, dou
   const double* T = ft(F, i, k);
   if (r == 0) return;
   if (r < 0) {
-    apply_ts_reflector(colmajor(const_cast<double*>(Y), b), b, b, T, Ck, ldc, colmajor(Ci, (int)ldc), nc,
+    apply_ts_reflector<double>(colmajor(const_cast<double*>(Y), b), b, b, T, Ck, ldc, colmajor(Ci, (int)ldc), nc,
                        trans, c);
     return;
   }
@@ -47,7 +47,7 @@ __device__ void apply_ts_tile(const FactorView& F, int i, int k, double* Ck, dou
   gemm(r, nc, b, 1.0, Y, b, true, Ci, ldc, false, 0.0, Pm, r, c);
   copy_mat(P0, r, Pm, r, r, nc);
   __syncthreads();
-  apply_ts_reflector(rowmajor(const_cast<double*>(Y) + (size_t)b * F.cap, b), r, b, T, Ck, ldc,
+  apply_ts_reflector<double>(rowmajor(const_cast<double*>(Y) + (size_t)b * F.cap, b), r, b, T, Ck, ldc,
                      colmajor(Pm, r), nc, trans, c);
   for (int e = threadIdx.x; e < r * nc; e += BLR_NT) Pm[e] -= P0[e];
   __syncthreads();
@@ -69,7 +69,7 @@ __global__ void __launch_bounds__(BLR_NT, 1) k_apply_q(FactorView F, double* B, 
   const int b = F.b;
   if (trans) {
     for (int k = 0; k < F.q; k++) {
-      apply_q(ftile(F, k, k), b, b, b, ft(F, k, k), Bc + (size_t)k * b, ldb, nc, true, c);
+      apply_q<double>(ftile(F, k, k), b, b, b, ft(F, k, k), Bc + (size_t)k * b, ldb, nc, true, c);
       for (int i = k + 1; i < F.p; i++)
         apply_ts_tile(F, i, k, Bc + (size_t)k * b, Bc + (size_t)i * b, ldb, nc, true, scr, c);
     }
@@ -77,7 +77,7 @@ __global__ void __launch_bounds__(BLR_NT, 1) k_apply_q(FactorView F, double* B, 
     for (int k = F.q - 1; k >= 0; k--) {
       for (int i = F.p - 1; i > k; i--)
         apply_ts_tile(F, i, k, Bc + (size_t)k * b, Bc + (size_t)i * b, ldb, nc, false, scr, c);
-      apply_q(ftile(F, k, k), b, b, b, ft(F, k, k), Bc + (size_t)k * b, ldb, nc, false, c);
+      apply_q<double>(ftile(F, k, k), b, b, b, ft(F, k, k), Bc + (size_t)k * b, ldb, nc, false, c);
     }
   }
 }

@@ -238,3 +238,68 @@ def test_invalid_arguments_fail_loudly(lib):
         lib.blr_compress_dense(a, lib.blr_opts_default(b=40, tol=1e-8))   # b not a multiple of 32
     with pytest.raises(lib.BLRError):
         lib.blr_compress_dense(a, lib.blr_opts_default(b=32, tol=0.0))    # no tolerance, no rank
+
+
+# ---------------------------------------------------------------- mixed precision
+# FP32 trailing updates and recompression, FP64 panels.  Tolerances follow
+# from FP32 rounding (u = 6e-8) times the growth of a few hundred updates:
+# Orth <= 1e-6 (the mixed-precision target), Res <= 10 x the recompression
+# tolerance, R within 1e-5 of the FP64 oracle on well-conditioned inputs.
+
+@pytest.mark.parametrize("m,n,b,seed,dense,zero", CASES[:4])
+def test_mixed_precision_factor_close_to_oracle(lib, m, n, b, seed, dense, zero):
+    import torch
+    a = _mixed_blr(m, n, b, seed, dense, zero)
+    p, q = m // b, n // b
+    ref = O.compress(tiles_of(a, b), p, q, b, eps=1e-14)
+    ranks, tiles = oracle_to_lib(ref)
+    mat = lib.blr_matrix_import(m, n, b, ranks, tiles)
+    opts = lib.blr_opts_default(b=b, tol=1e-6, rec_tol=1e-6, precision=lib.BLR_PREC_MIXED)
+    fac = lib.blr_qr(mat, opts)
+    fo = O.blr_qr(ref, 1e-14)
+    rk, tl = lib.blr_matrix_export(fac)
+    r_g = lib_r_dense(rk, tl, p, q, b)
+    r_o = fo.r_dense()
+    assert np.linalg.norm(r_g - r_o) <= 1e-5 * np.linalg.norm(r_o)
+    at = ref.dense()
+    e = np.zeros((m, n))
+    e[:n] = np.eye(n)
+    q1 = lib.to_fortran(torch.from_numpy(e))
+    lib.blr_apply_qt(fac, q1, trans=1)
+    q1 = q1.cpu().numpy()
+    orth = np.linalg.norm(q1.T @ q1 - np.eye(n)) / np.sqrt(n)
+    res = np.linalg.norm(q1 @ r_g - at) / np.linalg.norm(at)
+    assert orth <= 1e-6
+    assert res <= 1e-5
+    fac.destroy()
+
+
+def test_mixed_precision_kernel_matrix(lib):
+    """Yukawa 3D, 4096 x 2048, b = 128, tol 1e-6: mixed Res against A within
+    10 x tol, Orth <= 1e-6, and the FP64 path on the same input agrees."""
+    import torch
+    pr = W.kernel_problem("yukawa3d", 4096, 2048, 128, 41, 42)
+    out = {}
+    for prec in (lib.BLR_PREC_FP64, lib.BLR_PREC_MIXED):
+        opts = lib.blr_opts_default(b=128, tol=1e-6, precision=prec)
+        mat = lib.blr_compress_kernel(pr.x, pr.y, "yukawa3d", opts)
+        fac = lib.blr_qr(mat, opts)
+        m, n = 4096, 2048
+        z = np.random.default_rng(3).standard_normal((n, 8))
+        rz = lib.blr_apply_r(fac, lib.to_fortran(torch.from_numpy(z)))
+        y = torch.zeros((8, m), dtype=torch.float64, device="cuda").t()
+        y[:n] = rz
+        lib.blr_apply_qt(fac, y, trans=1)
+        az = pr.dense() @ z
+        res = np.linalg.norm(y.cpu().numpy() - az) / np.linalg.norm(az)
+        e = np.zeros((m, 64))
+        e[:64, :64] = np.eye(64)
+        e[:n] = np.random.default_rng(4).standard_normal((n, 64))
+        qe = lib.to_fortran(torch.from_numpy(e))
+        lib.blr_apply_qt(fac, qe, trans=1)
+        lib.blr_apply_qt(fac, qe, trans=0)
+        orth_probe = np.linalg.norm(qe.cpu().numpy() - e) / np.linalg.norm(e)
+        out[prec] = (res, orth_probe)
+        fac.destroy()
+    assert out[lib.BLR_PREC_FP64][0] <= 1e-5 and out[lib.BLR_PREC_MIXED][0] <= 1e-5
+    assert out[lib.BLR_PREC_FP64][1] <= 1e-13 and out[lib.BLR_PREC_MIXED][1] <= 1e-6
