@@ -174,6 +174,26 @@ int blr_apply_qt(const blr_factor* f, double* b_dev, int ldb, int nrhs, int tran
                  void* stream);
 
 /*
+ * blr_apply_qt_noalloc -- the same operation as blr_apply_qt, for callers
+ * that cannot allocate device memory during the call (inside a stream
+ * capture that must stay allocation-free, under an application-owned pool
+ * that forbids cudaMalloc after start-up, or where the allocator's implicit
+ * synchronisation is unaffordable).  The paper has no counterpart: this is
+ * an interface variant of the Algorithm 5 apply.  Nothing is allocated: the
+ * scratch is a 4 MiB static device array inside the library, held by every
+ * GPU that loads it until the process exits.  Limit: the scratch must hold
+ * 256 bytes + q*8 bytes (rounded up to 256) + ceil(nrhs/8) * (16 (b/2) + 64)
+ * * 8 bytes; larger nrhs is rejected with BLR_ERR_INVALID (at b = 512, q = 64:
+ * up to 1008 right-hand sides).  The first call on a device looks up the
+ * array's device address (with that device current), so make it before any
+ * stream capture.  Every call shares the array: calls whose kernels overlap
+ * on the GPU race and must be serialised by the caller.  Arguments, layout
+ * and errors as blr_apply_qt.
+ */
+int blr_apply_qt_noalloc(const blr_factor* f, double* b_dev, int ldb, int nrhs, int trans,
+                         void* stream);
+
+/*
  * blr_lstsq -- least squares min ||A~ X - B||_F via the factor (QR used for
  * least squares, Section 1): X = R^{-1} (Q^T B)(1:n), then refine_steps
  * steps of X += R^{-1} Q_1^T (B - A X) with A = a_orig (BLR, FP64).

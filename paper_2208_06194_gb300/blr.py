@@ -61,6 +61,7 @@ _SIGS = {
     "blr_matrix_clone": (_I, [_P, ctypes.POINTER(_P), _P]),
     "blr_qr": (_I, [_P, ctypes.POINTER(Opts), ctypes.POINTER(_P), _P]),
     "blr_apply_qt": (_I, [_P, _P, _I, _I, _I, _P]),
+    "blr_apply_qt_noalloc": (_I, [_P, _P, _I, _I, _I, _P]),
     "blr_lstsq": (_I, [_P, _P, _P, _I, _P, _I, _I, _I, _P]),
     "blr_matmul": (_I, [_P, _P, _I, _P, _I, _I, _P]),
     "blr_apply_r": (_I, [_P, _P, _I, _P, _I, _I, _P]),
@@ -243,6 +244,13 @@ def blr_apply_qt(f: Factor, bmat, trans: int = 0, stream=None) -> None:
     """In place: trans=0 -> Q^T B, trans=1 -> Q B (B column-major m x nrhs)."""
     _check(lib().blr_apply_qt(f.handle, ctypes.c_void_p(bmat.data_ptr()), _ld(bmat), bmat.shape[1],
                               trans, _stream(stream)))
+
+
+def blr_apply_qt_noalloc(f: Factor, bmat, trans: int = 0, stream=None) -> None:
+    """blr_apply_qt without device allocation (static library scratch; see
+    include/blr.h for the size limit and the serialisation rule)."""
+    _check(lib().blr_apply_qt_noalloc(f.handle, ctypes.c_void_p(bmat.data_ptr()), _ld(bmat), bmat.shape[1],
+                                      trans, _stream(stream)))
 
 
 def blr_lstsq(f: Factor, bmat, a_orig: Matrix | None = None, refine_steps: int = 0, x=None, stream=None):

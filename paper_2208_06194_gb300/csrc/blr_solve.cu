@@ -347,3 +347,109 @@ extern "C" int blr_lstsq(const blr_factor* f, const blr_matrix* a_orig, const do
   if (dx) cudaFree(dx);
   return rc;
 }
+
+// ---------------------------------------------------------------------------
+// blr_apply_qt_noalloc: Q^T B / Q B without any device allocation.
+//
+// Some callers cannot allocate device memory at call time: code running
+// inside a stream capture that must not contain allocations, applications
+// with their own pool that forbids cudaMalloc after start-up, or latency-
+// critical solvers that cannot afford the allocator's implicit
+// synchronisation.  This entry point runs the same apply kernel as
+// blr_apply_qt, with its scratch (status word, per-block-column T offsets,
+// per-CTA work slabs) in the fixed array below instead of cudaMalloc'd
+// buffers.  The array is a file-scope device variable, so every GPU that
+// loads the library holds its 4 MiB until the process exits.  All calls on
+// a device share it and it keeps the previous call's contents; the call
+// clears the status word itself and every other byte it reads is written
+// first.  Calls whose kernels overlap on the GPU (different streams or
+// threads at the same time) race on this memory and must be serialised by
+// the caller.
+// ---------------------------------------------------------------------------
+#include <mutex>
+
+#define BLR_NOALLOC_BYTES (4u << 20)
+static __device__ __align__(256) double g_apply_scratch[BLR_NOALLOC_BYTES / sizeof(double)];
+
+namespace {
+
+__global__ void k_fill_toff(long long* toff, int p, int q) {
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < q; k += gridDim.x * blockDim.x)
+    toff[k] = (long long)k * p - (long long)k * (k - 1) / 2;   // sum_{k' < k} (p - k')
+}
+
+std::mutex g_noalloc_mu;
+double* g_noalloc_ptr[64];
+
+// Device address of the static scratch for the current device; looked up
+// once per device (with that device current) and cached.
+int noalloc_scratch(double** out) {
+  int dev = 0;
+  int rc = blr_cuda_check(cudaGetDevice(&dev), "cudaGetDevice");
+  if (rc) return rc;
+  if (dev < 0 || dev >= 64) {
+    blr_set_error("device ordinal %d out of range", dev);
+    return BLR_ERR_INVALID;
+  }
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_ptr[dev]) {
+    double* p = nullptr;
+    rc = blr_cuda_check(cudaGetSymbolAddress((void**)&p, g_apply_scratch), "cudaGetSymbolAddress");
+    if (rc) return rc;
+    g_noalloc_ptr[dev] = p;
+  }
+  *out = g_noalloc_ptr[dev];
+  return BLR_OK;
+}
+
+}  // namespace
+
+extern "C" int blr_apply_qt_noalloc(const blr_factor* f, double* b_dev, int ldb, int nrhs, int trans,
+                                    void* stream) {
+  if (!f || !b_dev) { blr_set_error("NULL argument"); return BLR_ERR_INVALID; }
+  if (ldb < f->a.m || nrhs < 0) { blr_set_error("bad ldb or nrhs"); return BLR_ERR_INVALID; }
+  if (nrhs == 0) return BLR_OK;
+  const blr_matrix& a = f->a;
+  const int nct = (nrhs + kColsPerCta - 1) / kColsPerCta;
+  const size_t slab = (size_t)2 * a.cap * kColsPerCta + 64;                // doubles per CTA
+  const size_t off_toff = 256, toff_bytes = (((size_t)a.q * sizeof(long long)) + 255) & ~(size_t)255;
+  const size_t off_slab = off_toff + toff_bytes;
+  const size_t need = off_slab + (size_t)nct * slab * sizeof(double);
+  if (need > BLR_NOALLOC_BYTES) {
+    const size_t max_ct = (BLR_NOALLOC_BYTES - off_slab) / (slab * sizeof(double));
+    blr_set_error("blr_apply_qt_noalloc: %d right-hand sides need %zu bytes of the %u-byte static scratch "
+                  "(at most %zu columns for b=%d, q=%d)", nrhs, need, BLR_NOALLOC_BYTES,
+                  max_ct * kColsPerCta, a.b, a.q);
+    return BLR_ERR_INVALID;
+  }
+  double* base = nullptr;
+  int rc = noalloc_scratch(&base);
+  if (!rc) rc = set_smem();
+  if (rc) return rc;
+  cudaStream_t st = (cudaStream_t)stream;
+  char* bytes = reinterpret_cast<char*>(base);
+  FactorView F{};
+  F.p = a.p; F.q = a.q; F.b = a.b; F.cap = a.cap;
+  F.tiles = a.tiles; F.rank = a.rank; F.t = f->t;
+  F.status = reinterpret_cast<int*>(bytes);
+  F.toff = reinterpret_cast<const long long*>(bytes + off_toff);
+  F.scratch = reinterpret_cast<double*>(bytes + off_slab);
+  F.slab = slab;
+  rc = blr_cuda_check(cudaMemsetAsync(F.status, 0, sizeof(int), st), "clear status");
+  if (rc) return rc;
+  k_fill_toff<<<1, 256, 0, st>>>(const_cast<long long*>(F.toff), a.p, a.q);
+  rc = blr_cuda_check(cudaGetLastError(), "launch k_fill_toff");
+  if (rc) return rc;
+  k_apply_q<<<nct, BLR_NT, BLR_SMEM_BYTES, st>>>(F, b_dev, ldb, nrhs, trans ? 0 : 1);
+  rc = blr_cuda_check(cudaGetLastError(), "launch k_apply_q");
+  if (rc) return rc;
+  int s = 0;
+  rc = blr_cuda_check(cudaMemcpyAsync(&s, F.status, sizeof(int), cudaMemcpyDeviceToHost, st), "read status");
+  if (!rc) rc = blr_cuda_check(cudaStreamSynchronize(st), "blr_apply_qt_noalloc");
+  if (rc) return rc;
+  if (s & ST_NUMERIC) {
+    blr_set_error("blr_apply_qt_noalloc: non-finite value");
+    return BLR_ERR_NUMERIC;
+  }
+  return BLR_OK;
+}
