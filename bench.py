@@ -153,6 +153,19 @@ def probes(blr, fac, a_clone, pr, torch, dev, k=16, seed=5):
 _SAMPLE = {}
 
 
+def tpmqrt_kinds(st):
+    """Trapezoidal updates by operand kinds (D dense, L low-rank) of Y~_ik,
+    R_kj and A_ij: count, summed CTA-seconds, counted GFLOP."""
+    out = {}
+    for v in range(8):
+        n = st["tpmqrt_kind"][v]
+        if n:
+            name = "Y{} R{} A{}".format(*("D" if v & bit else "L" for bit in (4, 2, 1)))
+            out[name] = {"n": n, "cta_s": round(st["tpmqrt_kind_seconds"][v], 3),
+                         "gflop": round(st["tpmqrt_kind_flops"][v] / 1e9, 1)}
+    return out
+
+
 def cpu_baseline(pr_args, tol):
     """The oracle as it stands on the host cores, on a bounded sample: the
     leading 16 x 2 tiles of the same matrix (compressed once by the oracle,
@@ -357,6 +370,7 @@ def main():
                   "after": {"n_dense": st["n_dense"], "mean": st["mean_rank"], "max": st["max_rank"]}},
         "kernel_seconds": k_sec,
         "task_cta_seconds": dict(zip(["geqrt", "larfb", "tsqrt", "tpmqrt"], st["task_seconds"])),
+        "tpmqrt_kinds": tpmqrt_kinds(st),
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak, "traffic": None,
                      "peak_note": ("FP64 ALU nominal 1.26 TFLOP/s (152 SMs x 2 DFMA/clk x 2.07 GHz)"

@@ -89,6 +89,10 @@ typedef struct blr_stats_t {
   long long tasks[4];       /* factor only: tasks executed per type */
   double task_seconds[4];   /* factor only: summed task durations per type (CTA-seconds) */
   double seconds;           /* factor only: device time of the factorization kernel */
+  long long tpmqrt_kind[8]; /* factor only: trapezoidal updates by operand kinds, index
+                               4 (Y~_ik dense) + 2 (R_kj dense) + (A_ij dense) at task start */
+  double tpmqrt_kind_seconds[8]; /* factor only: their summed durations (CTA-seconds) */
+  double tpmqrt_kind_flops[8];   /* factor only: their counted FP ops */
 } blr_stats_t;
 
 /* Fills *opts with the defaults (b = 512, tol = 1e-8, FP64). */

@@ -41,7 +41,9 @@ class Stats(ctypes.Structure):
                 ("q", ctypes.c_int), ("n_dense", ctypes.c_int), ("max_rank", ctypes.c_int),
                 ("mean_rank", ctypes.c_double), ("device_bytes", ctypes.c_longlong),
                 ("flops", ctypes.c_double * 5), ("tasks", ctypes.c_longlong * 4),
-                ("task_seconds", ctypes.c_double * 4), ("seconds", ctypes.c_double)]
+                ("task_seconds", ctypes.c_double * 4), ("seconds", ctypes.c_double),
+                ("tpmqrt_kind", ctypes.c_longlong * 8), ("tpmqrt_kind_seconds", ctypes.c_double * 8),
+                ("tpmqrt_kind_flops", ctypes.c_double * 8)]
 
 
 _lib = None
@@ -291,6 +293,8 @@ def blr_stats(obj) -> dict:
     d["flops"] = list(s.flops)
     d["tasks"] = list(s.tasks)
     d["task_seconds"] = list(s.task_seconds)
+    for k in ("tpmqrt_kind", "tpmqrt_kind_seconds", "tpmqrt_kind_flops"):
+        d[k] = list(getattr(s, k))
     return d
 
 

@@ -283,6 +283,11 @@ extern "C" int blr_stats(const void* handle, int handle_is_factor, blr_stats_t* 
     for (int t = 0; t < 4; t++) out->tasks[t] = f->tasks[t];
     for (int t = 0; t < 4; t++) out->task_seconds[t] = f->task_seconds[t];
     out->seconds = f->seconds;
+    for (int v = 0; v < 8; v++) {
+      out->tpmqrt_kind[v] = f->tpmqrt_kind[v];
+      out->tpmqrt_kind_seconds[v] = f->tpmqrt_kind_seconds[v];
+      out->tpmqrt_kind_flops[v] = f->tpmqrt_kind_flops[v];
+    }
   }
   return BLR_OK;
 }

@@ -1,604 +1,12 @@
-// Tiled Householder BLR-QR (Algorithm 4 with the BLR tile kernels of
-// Section 3.4) as one persistent device-side task scheduler (Section 4.3).
-//
-// Storage: tile (i,j) owns b*b doubles; a dense tile is b x b column-major;
-// a low-rank tile of rank r keeps U (b x r) at offset 0 and V (b x r) at
-// offset b*(b/2).  After the factorization tile (i,k), i > k, holds
-// Y~_ik = U_ik Y_ik with Y_ik^T in the V slot (Section 3.4.3), or a dense
-// Y_ik.  Every reflector block is kept in compact-WY form with inner
-// blocking: the T of each 32 consecutive reflectors (Eq. 3, Eq. 21).
+// Host side of blr_qr: builds the scheduler state of the tile DAG of
+// Algorithm 4 and launches the persistent kernel (blr_factor_fp64.cu,
+// blr_factor_mixed.cu); plus the host-only check of the DAG formulas.
 #include <cstdio>
 #include <cstdlib>
 #include <algorithm>
 #include <vector>
-#include "blr_device.cuh"
+#include "blr_internal.h"
 #include "blr_dag.h"
-
-namespace {
-
-// Bump allocator over the CTA's private scratch slab.  The slab holds
-// BLR_SLAB_B2 * b^2 doubles, more than any task needs, and no single request
-// exceeds 2 b^2; should the total ever run over, the request is served from
-// the slab's start (still in bounds) and the overflow flag fails the call.
-struct TaskEnv {
-  const SchedParams* P;
-  double* slab;
-  size_t used;
-  bool overflow;
-  __device__ double* alloc(size_t n) {
-    const size_t nn = (n + 31) & ~(size_t)31;   // 256-byte granules
-    if (used + nn > P->slab) {
-      overflow = true;
-      return slab;
-    }
-    double* p = slab + used;
-    used += nn;
-    return p;
-  }
-};
-
-__device__ __forceinline__ double* tile_ptr(const SchedParams& P, int i, int j) {
-  return P.tiles + ((size_t)j * P.p + i) * (size_t)P.b * P.b;
-}
-__device__ __forceinline__ int* rank_ptr(const SchedParams& P, int i, int j) {
-  return P.rank + (size_t)j * P.p + i;
-}
-__device__ __forceinline__ double* t_ptr(const SchedParams& P, int i, int k) {
-  return P.t + (size_t)(P.toff_dev[k] + (i - k)) * BLR_NB * P.b;
-}
-__device__ __forceinline__ int ld_rank(const int* p) { return __ldcg(p); }
-
-// ---------------------------------------------------------------------------
-// TSQRT panel: Householder on [Rp (w x w upper, ld NB); Bp (ry x w, ld ldb)],
-// reflector j = [e_j; y_j] (Section 3.4.3).  Always FP64.
-// ---------------------------------------------------------------------------
-__device__ void ts_panel_qr(double* Rp, double* Bp, int ldb, int ry, int w, double* tau, Ctx& c) {
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  __syncthreads();
-  for (int j = 0; j < w; j++) {
-    double part = 0.0;
-    for (int s = threadIdx.x; s < ry; s += BLR_NT) {
-      double x = Bp[s + j * ldb];
-      part += x * x;
-    }
-    double sig2 = block_sum(part, c.s.red);
-    if (threadIdx.x == 0) {
-      double beta, tj, sc;
-      house(Rp[j + j * BLR_NB], sig2, beta, tj, sc);
-      flag_numeric(c, beta);
-      c.s.scal[0] = beta;
-      c.s.scal[1] = tj;
-      c.s.scal[2] = sc;
-    }
-    __syncthreads();
-    const double tj = c.s.scal[1], sc = c.s.scal[2];
-    for (int s = threadIdx.x; s < ry; s += BLR_NT) Bp[s + j * ldb] *= sc;
-    __syncthreads();
-    for (int l = j + 1 + warp; l < w; l += BLR_NWARP) {
-      double acc = 0.0;
-      for (int s = lane; s < ry; s += 32) acc += Bp[s + j * ldb] * Bp[s + l * ldb];
-      acc = warp_sum(acc);
-      double wl = (__shfl_sync(FULLMASK, Rp[j + l * BLR_NB], 0) + acc) * tj;
-      if (lane == 0) Rp[j + l * BLR_NB] -= wl;
-      for (int s = lane; s < ry; s += 32) Bp[s + l * ldb] -= wl * Bp[s + j * ldb];
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      Rp[j + j * BLR_NB] = c.s.scal[0];
-      tau[j] = tj;
-    }
-    __syncthreads();
-  }
-  c.fma += (double)ry * w * w;
-}
-
-// ---------------------------------------------------------------------------
-// Rounded addition (Algorithm 6) for C = Uf H0^T where H has already been
-// QR-factored in place (R_H in its top s x s, reflectors below, T blocks TH):
-// QR(Uf) = Q_U R_U, core M = R_U R_H^T (s x s), then a truncated
-// column-pivoted QR of the core, M P = Q_M R_M, stopped at the smallest r
-// with ||R_M(r:,r:)||_F <= eps ||M||_F.  Because ||C - C_r||_F equals the
-// core's truncation error, the result meets Algorithm 6's bound
-// ||C - U_C V_C^T||_F <= eps ||C||_F; U_C = Q_U Q_M [I_r; 0] is orthonormal
-// and V_C = Q_H [P R_M(0:r,:)^T; 0].  (Algorithm 6 truncates the core's SVD;
-// the pivoted QR reaches the same error bound in O(s^2 r) work instead of
-// O(s^3) per Jacobi sweep, with a rank that can exceed the optimal one by a
-// few.)  Uf is overwritten.  The result goes to dest in tile layout (U at 0,
-// V at b*cap); one whose rank would exceed dense_rank is written dense as
-// the product Uf0 H0^T.  Arithmetic in S.
-// ---------------------------------------------------------------------------
-template <class S>
-__device__ void recompress_side(TaskEnv& env, S* Uf, int ldu, const S* H, const S* TH, const S* H0, int s,
-                                S* dest, int* dest_rank, Ctx& c) {
-  const SchedParams& P = *env.P;
-  const int b = P.b;
-  const size_t mark = env.used;
-  if (s == 0) {
-    if (threadIdx.x == 0) *dest_rank = 0;
-    __syncthreads();
-    return;
-  }
-  S* U0 = (S*)env.alloc(((size_t)b * s * sizeof(S) + 7) / 8);
-  copy_mat(U0, b, Uf, ldu, b, s);
-  S* TU = (S*)env.alloc(((size_t)BLR_NB * s * sizeof(S) + 7) / 8);
-  __syncthreads();
-  geqrf(Uf, ldu, b, s, TU, c);
-  S* RU = (S*)env.alloc(((size_t)s * s * sizeof(S) + 7) / 8);
-  S* RH = (S*)env.alloc(((size_t)s * s * sizeof(S) + 7) / 8);
-  for (int e = threadIdx.x; e < s * s; e += BLR_NT) {
-    int a = e % s, l = e / s;
-    RU[e] = (a <= l) ? ldg(Uf + a + (size_t)l * ldu) : S(0);
-    RH[e] = (a <= l) ? ldg(H + a + (size_t)l * b) : S(0);
-  }
-  __syncthreads();
-  S* M = (S*)env.alloc(((size_t)s * s * sizeof(S) + 7) / 8);
-  gemm(s, s, s, S(1), RU, s, false, RH, s, true, S(0), M, s, c);
-  double part = 0.0;
-  for (int e = threadIdx.x; e < s * s; e += BLR_NT) part += (double)M[e] * (double)M[e];
-  const double nrm2 = block_sum(part, c.s.red);
-  const double tol2 = P.rec_tol * P.rec_tol * nrm2;
-  S* tauM = (S*)env.alloc(((size_t)s * sizeof(S) + 7) / 8);
-  int* perm = c.s.ivec;
-  const int r = qrcp(M, s, s, s, tol2, P.dense_rank, perm, tauM, c.s.flag + 2, c);
-  const int over = c.s.flag[2];
-  __syncthreads();
-  if (over) {
-    gemm(b, b, s, S(1), U0, b, false, H0, b, true, S(0), dest, b, c);
-    __syncthreads();
-    if (threadIdx.x == 0) *dest_rank = -1;
-    __syncthreads();
-    env.used = mark;
-    return;
-  }
-  if (r > 0) {
-    S* CU = (S*)env.alloc(((size_t)b * r * sizeof(S) + 7) / 8);
-    S* CV = (S*)env.alloc(((size_t)b * r * sizeof(S) + 7) / 8);
-    zero_mat(CU, b, b, r);
-    zero_mat(CV, b, b, r);
-    __syncthreads();
-    for (int l = threadIdx.x; l < r; l += BLR_NT) CU[l + (size_t)l * b] = S(1);
-    for (int e = threadIdx.x; e < s * r; e += BLR_NT) {
-      int cc = e % s, l = e / s;
-      CV[perm[cc] + (size_t)l * b] = (cc >= l) ? M[l + (size_t)cc * s] : S(0);
-    }
-    __syncthreads();
-    apply_q_unblocked(M, s, s, r, tauM, CU, b, r, false, c);
-    apply_q<S>(Uf, ldu, b, s, TU, CU, b, r, false, c);
-    apply_q<S>(H, b, b, s, TH, CV, b, r, false, c);
-    copy_mat(dest, b, CU, b, b, r);
-    copy_mat(dest + (size_t)b * P.cap, b, CV, b, b, r);
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) *dest_rank = r;
-  __syncthreads();
-  env.used = mark;
-}
-
-// ---------------------------------------------------------------------------
-// Task bodies.  S is the arithmetic of the trailing compact-WY updates and of
-// the recompressions: double on the FP64 path, float on the mixed path.
-// Panel factorizations (Householder norms, tau, vectors, T) are FP64 on both.
-// ---------------------------------------------------------------------------
-
-// GEQRT(k): Householder QR of the dense diagonal tile (Section 3.4.1).
-template <class S>
-__device__ void task_geqrt(TaskEnv& env, int k, Ctx& c) {
-  const SchedParams& P = *env.P;
-  const int b = P.b;
-  double* A = tile_ptr(P, k, k);
-  double* Tp = t_ptr(P, k, k);
-  if (std::is_same<S, double>::value) {
-    geqrf(A, b, b, b, Tp, c);
-    return;
-  }
-  double* pnl = c.s.pnl;
-  for (int c0 = 0; c0 < b; c0 += BLR_NB) {
-    const int w = BLR_NB, h = b - c0, ldp = h | 1;
-    __syncthreads();
-    stage_in(pnl, ldp, colmajor(A + c0 + (size_t)c0 * b, b), h, w);
-    panel_qr(pnl, ldp, h, w, c.s.tau, c);
-    gram_panel(pnl, ldp, h, w, c.s.z, c);
-    t_recur(c.s.z, c.s.tau, w, c.s.t, c);
-    for (int e = threadIdx.x; e < BLR_NB * BLR_NB; e += BLR_NT) Tp[e + (size_t)c0 * BLR_NB] = c.s.t[e];
-    stage_out(colmajor(A + c0 + (size_t)c0 * b, b), pnl, ldp, h, w);
-    __syncthreads();
-    if (c0 + w < b) {
-      const int ldq = stage_panel<S>(A, b, b, c0, w, Tp, c);
-      apply_refl_panel(A + c0 + (size_t)(c0 + w) * b, b, h, b - c0 - w, (const S*)as<S>(c.s.pnl), ldq, w,
-                       (const S*)as<S>(c.s.t), true, c);
-    }
-  }
-}
-
-// LARFB(k,j): R_kj = Q_kk^T A_kj (Section 3.4.2): U <- Q^T U, or the dense tile.
-template <class S>
-__device__ void task_larfb(TaskEnv& env, int k, int j, Ctx& c) {
-  const SchedParams& P = *env.P;
-  const int b = P.b;
-  const int r = ld_rank(rank_ptr(P, k, j));
-  double* C = tile_ptr(P, k, j);
-  const int nc = (r < 0) ? b : r;
-  if (nc > 0) apply_q<S>(tile_ptr(P, k, k), b, b, b, t_ptr(P, k, k), C, b, nc, true, c);
-}
-
-// TSQRT(i,k): QR([R_kk; A^V_ik]) with A^V = V^T (low-rank) or the dense tile
-// (Section 3.4.3, Eqs. 19-21); Y_ik overwrites A^V in place.  The panel
-// factorization is FP64; the update of the trailing columns runs in S.
-template <class S>
-__device__ void task_tsqrt(TaskEnv& env, int i, int k, Ctx& c) {
-  const SchedParams& P = *env.P;
-  const int b = P.b;
-  const int r = ld_rank(rank_ptr(P, i, k));
-  double* R = tile_ptr(P, k, k);
-  double* Tk = t_ptr(P, i, k);
-  double* B = tile_ptr(P, i, k);
-  const int ry = (r < 0) ? b : r;
-  View<double> Bv = (r < 0) ? colmajor(B, b) : rowmajor(B + (size_t)b * P.cap, b);
-  if (ry == 0) {
-    for (int e = threadIdx.x; e < BLR_NB * b; e += BLR_NT) Tk[e] = 0.0;
-    __syncthreads();
-    return;
-  }
-  for (int c0 = 0; c0 < b; c0 += BLR_NB) {
-    const int w = BLR_NB;
-    const int ldb = ry | 1;
-    __syncthreads();
-    for (int e = threadIdx.x; e < w * w; e += BLR_NT) {
-      int a = e % w, l = e / w;
-      c.s.rp[a + l * BLR_NB] = (a <= l) ? ldg(R + (c0 + a) + (size_t)(c0 + l) * b) : 0.0;
-    }
-    View<double> Bp = Bv.shifted(0, c0);
-    stage_in(c.s.pnl, ldb, Bp, ry, w);
-    ts_panel_qr(c.s.rp, c.s.pnl, ldb, ry, w, c.s.tau, c);
-    gram_dense(c.s.pnl, ldb, ry, w, c.s.z, c);
-    t_recur(c.s.z, c.s.tau, w, c.s.t, c);
-    for (int e = threadIdx.x; e < BLR_NB * BLR_NB; e += BLR_NT) Tk[e + (size_t)c0 * BLR_NB] = c.s.t[e];
-    for (int e = threadIdx.x; e < w * w; e += BLR_NT) {
-      int a = e % w, l = e / w;
-      if (a <= l) R[(c0 + a) + (size_t)(c0 + l) * b] = c.s.rp[a + l * BLR_NB];
-    }
-    stage_out(Bp, c.s.pnl, ldb, ry, w);
-    __syncthreads();
-    if (c0 + w < b) {
-      View<double> Cb = Bv.shifted(0, c0 + w);
-      if (std::is_same<S, double>::value) {
-        apply_refl_ts(R + c0 + (size_t)(c0 + w) * b, b, Cb, ry, b - c0 - w, c.s.pnl, ldb, w, c.s.t, true, c);
-      } else {
-        const int ldy = stage_reflector_panel<S>(Bv, ry, c0, w, Tk, c);
-        apply_refl_ts(R + c0 + (size_t)(c0 + w) * b, b, Cb, ry, b - c0 - w, (const S*)as<S>(c.s.pnl), ldy, w,
-                      (const S*)as<S>(c.s.t), true, c);
-      }
-    }
-    __syncthreads();
-  }
-}
-
-// TPMQRT(i,j,k): [R_kj; A_ij] <- Q_ik^T [R_kj; A_ij] with
-// Q_ik = I - [I; Y~] T [I; Y~]^T (Section 3.4.4).  With Y~ = U_ik Y_ik the
-// operator acts on A_ij only through P = U_ik^T A_ij, so it is applied to
-// the reduced pair [R_kj; P] (rows b + r_Y) and A_ij += U_ik (P' - P).  When
-// R_kj and A_ij are low-rank the pair is kept factored, [R; P] = G H^T, the
-// reflector is applied to G, and both results are recompressed by the
-// rounded addition of Algorithm 6 (sharing the QR of H).
-//
-// Operands are tile-layout buffers of type S (U at 0, V at b*cap, or dense
-// b x b); rY/rR/rA are their ranks (-1 dense); new ranks go to *nR, *nA.
-template <class S>
-__device__ void tpmqrt_core(TaskEnv& env, S* Yt, int rY, const S* Tik, S* Rt, int rR, S* At, int rA, int* nR,
-                            int* nA, Ctx& c) {
-  const SchedParams& P = *env.P;
-  const int b = P.b, cap = P.cap;
-  auto alloc = [&](size_t n) { return (S*)env.alloc((n * sizeof(S) + 7) / 8); };
-  const bool ylr = rY >= 0;
-  if (ylr && rY == 0) return;           // the reflector is the identity
-  const int ry = ylr ? rY : b;
-  S* Uy = Yt;
-  View<S> Yr = ylr ? rowmajor(Yt + (size_t)b * cap, b) : colmajor(Yt, b);
-
-  if (rR >= 0 && (rA >= 0 || ylr)) {
-    // ---------------- factored paths -----------------
-    const bool adense = rA < 0;         // A dense, Y low-rank
-    const int s2 = adense ? ry : rA;    // columns of the P part
-    const int s = rR + s2;
-    if (s == 0) return;
-    const int ldG = b + ry;
-    S* G = alloc((size_t)ldG * s);
-    S* H = alloc((size_t)b * s);
-    S* H0 = alloc((size_t)b * s);
-    S* PU0 = alloc((size_t)ry * s2);
-    zero_mat(G, ldG, ldG, s);
-    __syncthreads();
-    copy_mat(G, ldG, Rt, b, b, rR);                              // U_R
-    copy_mat(H, b, Rt + (size_t)b * cap, b, b, rR);              // V_R
-    if (!adense) {
-      if (ylr) gemm(ry, rA, b, S(1), Uy, b, true, At, b, false, S(0), G + b + (size_t)rR * ldG, ldG, c);
-      else copy_mat(G + b + (size_t)rR * ldG, ldG, At, b, b, rA);
-      copy_mat(H + (size_t)rR * b, b, At + (size_t)b * cap, b, b, rA);
-    } else {
-      gemm(b, ry, b, S(1), At, b, true, Uy, b, false, S(0), H + (size_t)rR * b, b, c);
-      __syncthreads();
-      for (int e = threadIdx.x; e < ry; e += BLR_NT) G[b + e + (size_t)(rR + e) * ldG] = S(1);
-    }
-    __syncthreads();
-    copy_mat(PU0, ry, G + b + (size_t)rR * ldG, ldG, ry, s2);
-    copy_mat(H0, b, H, b, b, s);
-    __syncthreads();
-    apply_ts_reflector<S>(Yr, ry, b, Tik, G, ldG, colmajor(G + b, ldG), s, true, c);
-    for (int e = threadIdx.x; e < ry * s2; e += BLR_NT) {
-      int a = e % ry, l = e / ry;
-      G[b + a + (size_t)(rR + l) * ldG] -= PU0[e];
-    }
-    __syncthreads();
-    S* TH = alloc((size_t)BLR_NB * s);
-    if (!adense) {
-      S* UfA = alloc((size_t)b * s);
-      if (ylr) gemm(b, s, ry, S(1), Uy, b, false, G + b, ldG, false, S(0), UfA, b, c);
-      else copy_mat(UfA, b, G + b, ldG, b, s);
-      __syncthreads();
-      for (int e = threadIdx.x; e < b * rA; e += BLR_NT) {
-        int a = e % b, l = e / b;
-        UfA[a + (size_t)(rR + l) * b] += ldg(At + a + (size_t)l * b);
-      }
-      __syncthreads();
-      geqrf(H, b, b, s, TH, c);
-      recompress_side(env, G, ldG, H, TH, H0, s, Rt, nR, c);
-      recompress_side(env, UfA, b, H, TH, H0, s, At, nA, c);
-    } else {
-      S* M1 = alloc((size_t)b * s);
-      gemm(b, s, ry, S(1), Uy, b, false, G + b, ldG, false, S(0), M1, b, c);
-      gemm(b, b, s, S(1), M1, b, false, H0, b, true, S(1), At, b, c);
-      geqrf(H, b, b, s, TH, c);
-      recompress_side(env, G, ldG, H, TH, H0, s, Rt, nR, c);
-    }
-    return;
-  }
-
-  // ---------------- dense path: R_kj dense (or becomes dense) -----------------
-  S* Rd;
-  bool r_scratch = false;
-  if (rR < 0) {
-    Rd = Rt;
-  } else {
-    Rd = alloc((size_t)b * b);
-    if (rR > 0) gemm(b, b, rR, S(1), Rt, b, false, Rt + (size_t)b * cap, b, true, S(0), Rd, b, c);
-    else zero_mat(Rd, b, b, b);
-    r_scratch = true;
-  }
-  S* Pm;
-  int ldp;
-  S* P0 = nullptr;
-  bool a_inplace = false;
-  if (ylr) {
-    ldp = ry;
-    Pm = alloc((size_t)ry * b);
-    if (rA < 0) {
-      gemm(ry, b, b, S(1), Uy, b, true, At, b, false, S(0), Pm, ry, c);
-    } else if (rA == 0) {
-      zero_mat(Pm, ry, ry, b);
-    } else {
-      S* PU = alloc((size_t)ry * rA);
-      gemm(ry, rA, b, S(1), Uy, b, true, At, b, false, S(0), PU, ry, c);
-      gemm(ry, b, rA, S(1), PU, ry, false, At + (size_t)b * cap, b, true, S(0), Pm, ry, c);
-    }
-    P0 = alloc((size_t)ry * b);
-    __syncthreads();
-    copy_mat(P0, ry, Pm, ry, ry, b);
-  } else {
-    ldp = b;
-    if (rA < 0) {
-      Pm = At;
-      a_inplace = true;
-    } else {
-      Pm = alloc((size_t)b * b);
-      if (rA > 0) gemm(b, b, rA, S(1), At, b, false, At + (size_t)b * cap, b, true, S(0), Pm, b, c);
-      else zero_mat(Pm, b, b, b);
-    }
-  }
-  __syncthreads();
-  apply_ts_reflector<S>(Yr, ry, b, Tik, Rd, b, colmajor(Pm, ldp), b, true, c);
-  if (r_scratch) {
-    copy_mat(Rt, b, Rd, b, b, b);
-    __syncthreads();
-    if (threadIdx.x == 0) *nR = -1;
-  }
-  __syncthreads();
-  if (!ylr) {
-    if (!a_inplace) {
-      copy_mat(At, b, Pm, b, b, b);
-      __syncthreads();
-      if (threadIdx.x == 0) *nA = -1;
-    }
-    __syncthreads();
-    return;
-  }
-  for (int e = threadIdx.x; e < ry * b; e += BLR_NT) Pm[e] -= P0[e];
-  __syncthreads();
-  if (rA < 0) {
-    gemm(b, b, ry, S(1), Uy, b, false, Pm, ry, false, S(1), At, b, c);
-    return;
-  }
-  const int s = rA + ry;
-  S* Uf = alloc((size_t)b * s);
-  S* H = alloc((size_t)b * s);
-  S* H0 = alloc((size_t)b * s);
-  copy_mat(Uf, b, At, b, b, rA);
-  copy_mat(Uf + (size_t)rA * b, b, Uy, b, b, ry);
-  copy_mat(H, b, At + (size_t)b * cap, b, b, rA);
-  __syncthreads();
-  for (int e = threadIdx.x; e < b * ry; e += BLR_NT) {
-    int a = e % b, l = e / b;
-    H[a + (size_t)(rA + l) * b] = Pm[l + (size_t)a * ldp];
-  }
-  __syncthreads();
-  copy_mat(H0, b, H, b, b, s);
-  S* TH = alloc((size_t)BLR_NB * s);
-  __syncthreads();
-  geqrf(H, b, b, s, TH, c);
-  recompress_side(env, Uf, b, H, TH, H0, s, At, nA, c);
-}
-
-// Copies the live part of a tile (rank r: U and V columns; -1: dense) between
-// storage types.
-template <class D, class Src>
-__device__ void copy_tile(D* dst, const Src* src, int r, int b, int cap) {
-  if (r < 0) {
-    copy_mat(dst, b, src, b, b, b);
-  } else if (r > 0) {
-    copy_mat(dst, b, src, b, b, r);
-    copy_mat(dst + (size_t)b * cap, b, src + (size_t)b * cap, b, b, r);
-  }
-}
-
-template <class S>
-__device__ void task_tpmqrt(TaskEnv& env, int i, int j, int k, Ctx& c) {
-  const SchedParams& P = *env.P;
-  const int b = P.b, cap = P.cap;
-  const int rY = ld_rank(rank_ptr(P, i, k));
-  const int rR = ld_rank(rank_ptr(P, k, j));
-  const int rA = ld_rank(rank_ptr(P, i, j));
-  double* Yt = tile_ptr(P, i, k);
-  double* Rt = tile_ptr(P, k, j);
-  double* At = tile_ptr(P, i, j);
-  const double* Tik = t_ptr(P, i, k);
-  if (std::is_same<S, double>::value) {
-    tpmqrt_core<double>(env, Yt, rY, Tik, Rt, rR, At, rA, rank_ptr(P, k, j), rank_ptr(P, i, j), c);
-    return;
-  }
-  if (rY == 0) return;
-  // mixed: FP32 copies of the operands, FP32 arithmetic, results back to FP64
-  float* Yf = (float*)env.alloc((size_t)b * b / 2);
-  float* Tf = (float*)env.alloc((size_t)BLR_NB * b / 2);
-  float* Rf = (float*)env.alloc((size_t)b * b / 2);
-  float* Af = (float*)env.alloc((size_t)b * b / 2);
-  copy_tile(Yf, Yt, rY, b, cap);
-  copy_mat(Tf, BLR_NB, Tik, BLR_NB, BLR_NB, b);
-  copy_tile(Rf, Rt, rR, b, cap);
-  copy_tile(Af, At, rA, b, cap);
-  __shared__ int newr[2];
-  if (threadIdx.x == 0) { newr[0] = rR; newr[1] = rA; }
-  __syncthreads();
-  tpmqrt_core<float>(env, Yf, rY, Tf, Rf, rR, Af, rA, &newr[0], &newr[1], c);
-  __syncthreads();
-  const int r1 = newr[0], r2 = newr[1];
-  copy_tile(Rt, Rf, r1, b, cap);
-  copy_tile(At, Af, r2, b, cap);
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    *rank_ptr(P, k, j) = r1;
-    *rank_ptr(P, i, j) = r2;
-  }
-  __syncthreads();
-}
-
-// ---------------------------------------------------------------------------
-// Persistent scheduler
-// ---------------------------------------------------------------------------
-__device__ __forceinline__ unsigned long long gtimer() {
-  unsigned long long t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
-}
-
-__device__ void q_push(const SchedParams& P, int qi, int task) {
-  int pos = atomicAdd(P.qtail + qi * 32, 1);
-  atomicExch(P.qbuf + (size_t)qi * P.n_tasks + pos, task);
-}
-
-// Thread 0 only.  Returns a task id, or -1 when the factorization is done
-// or aborted.  Every wait is bounded by the watchdog budget.
-__device__ int q_pop(const SchedParams& P) {
-  unsigned ns = 64;
-  while (true) {
-    if (*(volatile int*)P.status != 0) return -1;
-    for (int qi = 0; qi < BLR_NQ; qi++) {
-      volatile int* head = P.qhead + qi * 32;
-      volatile int* tail = P.qtail + qi * 32;
-      while (true) {
-        int h = *head, t = *tail;
-        if (h >= t) break;
-        if (atomicCAS((int*)head, h, h + 1) == h) {
-          volatile int* slot = P.qbuf + (size_t)qi * P.n_tasks + h;
-          int v;
-          unsigned long long t0 = gtimer();
-          while ((v = *slot) < 0) {
-            if (gtimer() - t0 > (unsigned long long)P.watchdog_ns) {
-              atomicOr(P.status, ST_TIMEOUT);
-              return -1;
-            }
-            __nanosleep(32);
-          }
-          __threadfence();
-          return v;
-        }
-      }
-    }
-    if (*(volatile int*)P.done >= P.n_tasks) return -1;
-    unsigned long long now = gtimer();
-    unsigned long long last = *(volatile unsigned long long*)P.progress_ns;
-    if (last == 0ull) {
-      atomicCAS(P.progress_ns, 0ull, now);
-    } else if (now > last && now - last > (unsigned long long)P.watchdog_ns) {
-      atomicOr(P.status, ST_TIMEOUT);
-      return -1;
-    }
-    __nanosleep(ns);
-    if (ns < 8192) ns <<= 1;
-  }
-}
-
-__global__ void __launch_bounds__(BLR_NT, 1) k_factor(SchedParams P) {
-  extern __shared__ double smem[];
-  __shared__ int task_sh;
-  Ctx c;
-  c.s = sm_carve(smem);
-  c.status = P.status;
-  DagShape d{P.p, P.q, P.off_larfb, P.off_tsqrt, P.off_tpmqrt};
-  TaskEnv env{&P, P.scratch + (size_t)blockIdx.x * P.slab, 0, false};
-  while (true) {
-    if (threadIdx.x == 0) task_sh = q_pop(P);
-    __syncthreads();
-    const int task = task_sh;
-    __syncthreads();
-    if (task < 0) break;
-    int i, j, k;
-    const int type = dag_decode(d, task, &i, &j, &k);
-    const unsigned long long t_start = gtimer();
-    c.fma = 0.0;
-    env.used = 0;
-    env.overflow = false;
-    const bool mixed = P.precision == BLR_PREC_MIXED;
-    switch (type) {
-      case TASK_GEQRT: mixed ? task_geqrt<float>(env, k, c) : task_geqrt<double>(env, k, c); break;
-      case TASK_LARFB: mixed ? task_larfb<float>(env, k, j, c) : task_larfb<double>(env, k, j, c); break;
-      case TASK_TSQRT: mixed ? task_tsqrt<float>(env, i, k, c) : task_tsqrt<double>(env, i, k, c); break;
-      case TASK_TPMQRT: mixed ? task_tpmqrt<float>(env, i, j, k, c) : task_tpmqrt<double>(env, i, j, k, c); break;
-      default:
-        if (threadIdx.x == 0) atomicOr(P.status, ST_BADTASK);
-        break;
-    }
-    if (env.overflow && threadIdx.x == 0) atomicOr(P.status, ST_RANK);
-    __threadfence();
-    __syncthreads();
-    if (threadIdx.x == 0 && type >= 0) {
-      dag_for_each_successor(d, type, i, j, k, [&](int sid) {
-        if (atomicSub(P.deps + sid, 1) == 1) {
-          __threadfence();
-          int si, sj, sk;
-          const int st = dag_decode(d, sid, &si, &sj, &sk);
-          q_push(P, dag_queue(st, si, sj, sk), sid);
-        }
-      });
-      atomicAdd(P.flops + type, 2.0 * c.fma);
-      atomicAdd(P.ntask + type, 1ull);
-      atomicAdd(P.tns + type, gtimer() - t_start);
-      atomicExch(P.progress_ns, gtimer());
-      __threadfence();
-      atomicAdd(P.done, 1);
-    }
-  }
-}
-
-}  // namespace
 
 // ---------------------------------------------------------------------------
 // Host side of blr_qr
@@ -632,7 +40,9 @@ int blr_launch_factor(blr_factor* f, const blr_opts* o, cudaStream_t st) {
                o_qh = take(sizeof(int) * 32 * BLR_NQ), o_qt = take(sizeof(int) * 32 * BLR_NQ),
                o_done = take(sizeof(int)), o_status = take(sizeof(int)),
                o_prog = take(sizeof(unsigned long long)), o_flops = take(sizeof(double) * 4),
-               o_ntask = take(sizeof(unsigned long long) * 4), o_tns = take(sizeof(unsigned long long) * 4);
+               o_ntask = take(sizeof(unsigned long long) * 4), o_tns = take(sizeof(unsigned long long) * 4),
+               o_nvar = take(sizeof(unsigned long long) * 8), o_tvar = take(sizeof(unsigned long long) * 8),
+               o_fvar = take(sizeof(double) * 8);
   char* base = nullptr;
   double* scratch = nullptr;
   if (cudaMalloc(&base, bytes) != cudaSuccess) { blr_set_error("blr_qr: out of device memory (scheduler state)"); return BLR_ERR_OOM; }
@@ -666,6 +76,9 @@ int blr_launch_factor(blr_factor* f, const blr_opts* o, cudaStream_t st) {
   P.flops = (double*)(base + o_flops);
   P.ntask = (unsigned long long*)(base + o_ntask);
   P.tns = (unsigned long long*)(base + o_tns);
+  P.nvar = (unsigned long long*)(base + o_nvar);
+  P.tvar = (unsigned long long*)(base + o_tvar);
+  P.fvar = (double*)(base + o_fvar);
 
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   do {
@@ -680,12 +93,11 @@ int blr_launch_factor(blr_factor* f, const blr_opts* o, cudaStream_t st) {
     int first = 0, one = 1;
     if ((rc = blr_cuda_check(cudaMemcpyAsync(P.qbuf, &first, sizeof(int), cudaMemcpyHostToDevice, st), "seed queue"))) break;
     if ((rc = blr_cuda_check(cudaMemcpyAsync(P.qtail, &one, sizeof(int), cudaMemcpyHostToDevice, st), "seed queue"))) break;
-    if ((rc = blr_cuda_check(cudaFuncSetAttribute(k_factor, cudaFuncAttributeMaxDynamicSharedMemorySize, BLR_SMEM_BYTES), "smem attribute"))) break;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
     cudaEventRecord(e0, st);
-    k_factor<<<ctas, BLR_NT, BLR_SMEM_BYTES, st>>>(P);
-    if ((rc = blr_cuda_check(cudaGetLastError(), "launch k_factor"))) break;
+    rc = (P.precision == BLR_PREC_MIXED) ? blr_run_factor_mixed(P, ctas, st) : blr_run_factor_fp64(P, ctas, st);
+    if (rc) break;
     cudaEventRecord(e1, st);
     if ((rc = blr_cuda_check(cudaStreamSynchronize(st), "k_factor"))) break;
     float ms = 0.f;
@@ -699,6 +111,16 @@ int blr_launch_factor(blr_factor* f, const blr_opts* o, cudaStream_t st) {
     cudaMemcpy(&done, P.done, sizeof(int), cudaMemcpyDeviceToHost);
     cudaMemcpy(fl, P.flops, sizeof(fl), cudaMemcpyDeviceToHost);
     cudaMemcpy(nt, P.ntask, sizeof(nt), cudaMemcpyDeviceToHost);
+    unsigned long long nv[8], tv[8];
+    double fv[8];
+    cudaMemcpy(nv, P.nvar, sizeof(nv), cudaMemcpyDeviceToHost);
+    cudaMemcpy(tv, P.tvar, sizeof(tv), cudaMemcpyDeviceToHost);
+    cudaMemcpy(fv, P.fvar, sizeof(fv), cudaMemcpyDeviceToHost);
+    for (int v = 0; v < 8; v++) {
+      f->tpmqrt_kind[v] = (long long)nv[v];
+      f->tpmqrt_kind_seconds[v] = tv[v] * 1e-9;
+      f->tpmqrt_kind_flops[v] = fv[v];
+    }
     f->flops[4] = 0;
     for (int t = 0; t < 4; t++) {
       f->flops[t] = fl[t];

@@ -56,6 +56,9 @@ struct blr_factor {
   double flops[5];
   long long tasks[4];
   double task_seconds[4];
+  long long tpmqrt_kind[8];
+  double tpmqrt_kind_seconds[8];
+  double tpmqrt_kind_flops[8];
   double seconds;
 };
 
@@ -84,6 +87,9 @@ struct SchedParams {
   double* flops;                 // 4 counters
   unsigned long long* ntask;     // 4 counters
   unsigned long long* tns;       // 4 counters: summed task durations (ns)
+  unsigned long long* nvar;      // 8 counters: updates per operand kind (4 Y dense + 2 R dense + A dense)
+  unsigned long long* tvar;      // 8 counters: their summed durations (ns)
+  double* fvar;                  // 8 counters: their counted flops
 };
 
 // host helpers (blr_api.cu)
@@ -93,6 +99,8 @@ int blr_num_sms();
 
 // kernel launchers implemented in the .cu files
 int blr_launch_factor(blr_factor* f, const blr_opts* o, cudaStream_t st);
+int blr_run_factor_fp64(const SchedParams& P, int ctas, cudaStream_t st);
+int blr_run_factor_mixed(const SchedParams& P, int ctas, cudaStream_t st);
 int blr_compress_impl(const double* a_dev, int lda, const double* x_dev, const double* y_dev,
                       int dim, int kernel_id, const double* scale_dev, int m, int n,
                       const blr_opts* o, blr_matrix* out, cudaStream_t st);
