@@ -232,6 +232,30 @@ int blr_stats(const void* handle, int handle_is_factor, blr_stats_t* out);
 void blr_destroy_matrix(blr_matrix* a);
 void blr_destroy_factor(blr_factor* f);
 
+/* ---- diagnostics ------------------------------------------------------- */
+
+/*
+ * blr_dag_selfcheck -- host only, no device work: builds the tile DAG of
+ * Algorithm 4 (Section 4.3) for p x q tiles from the scheduler's closed
+ * formulas, checks every in-degree, and runs the dependency-counter protocol
+ * in a seeded random order, checking that each task runs once, after its
+ * predecessors, and in each tile's writer order.  Returns 0 on success, or a
+ * positive code naming the first failed check (100: q > p or p, q < 1).
+ */
+int blr_dag_selfcheck(int p, int q, unsigned seed);
+
+/*
+ * blr_tc_gemm_selftest -- D = A B (device, column-major, FP64 in and out:
+ * A m x k, lda >= m; B k x n, ldb >= k; D m x n, ldd >= m) through the
+ * tensor-core building block of the mixed-precision updates (tcgen05 TF32
+ * MMAs on hi/lo splits of the operands, "3xTF32", FP32 accumulation in
+ * TMEM), one 128 x 256 tile of D per CTA.  The result has FP32 accuracy.
+ * Errors: BLR_ERR_INVALID, BLR_ERR_CUDA, BLR_ERR_TIMEOUT (a completion wait
+ * ran out; the kernel returns instead of hanging).
+ */
+int blr_tc_gemm_selftest(const double* a_dev, int lda, const double* b_dev, int ldb, double* d_dev,
+                         int ldd, int m, int n, int k, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -72,6 +72,7 @@ _SIGS = {
     "blr_destroy_matrix": (None, [_P]),
     "blr_destroy_factor": (None, [_P]),
     "blr_dag_selfcheck": (_I, [_I, _I, ctypes.c_uint]),
+    "blr_tc_gemm_selftest": (_I, [_P, _I, _P, _I, _P, _I, _I, _I, _I, _P]),
 }
 EXPORTED = tuple(_SIGS)
 
@@ -301,3 +302,16 @@ def blr_stats(obj) -> dict:
 def blr_dag_selfcheck(p: int, q: int, seed: int = 0) -> int:
     """Host-only check of the scheduler's DAG formulas (0 = pass)."""
     return lib().blr_dag_selfcheck(p, q, seed)
+
+
+def blr_tc_gemm_selftest(a, bm, stream=None):
+    """D = A B through the tensor-core building block (3xTF32, FP32
+    accumulation); a, bm are column-major float64 CUDA tensors."""
+    m, k = a.shape
+    k2, n = bm.shape
+    if k2 != k:
+        raise ValueError("inner dimensions differ")
+    d = fortran_empty(m, n, device=a.device)
+    _check(lib().blr_tc_gemm_selftest(a.data_ptr(), a.stride(1), bm.data_ptr(), bm.stride(1), d.data_ptr(),
+                                      d.stride(1), m, n, k, _stream(stream)))
+    return d

@@ -12,7 +12,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libblrqr.so")
 SOURCES = ["blr_api.cu", "blr_factor.cu", "blr_factor_fp64.cu", "blr_factor_mixed.cu", "blr_compress.cu",
-           "blr_solve.cu"]
+           "blr_solve.cu", "blr_tc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "--expt-relaxed-constexpr", "-Xcompiler", "-fPIC",
          "-I" + os.path.join(ROOT, "include"), "-I" + CSRC]

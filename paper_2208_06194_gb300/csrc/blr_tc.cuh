@@ -1,0 +1,278 @@
+// Fifth-generation tensor-core (tcgen05) building blocks for sm_103a: TMEM
+// allocation, shared-memory matrix descriptors, TF32 MMAs with FP32
+// accumulation in TMEM, completion through an mbarrier, and TMEM loads.
+//
+// Operand layout.  Both operands of D = A B^T are "K-major": row r of A
+// (M x K) and row n of B (N x K) hold consecutive K elements.  In shared
+// memory a K chunk of KC (= TC_KC) elements is stored in the no-swizzle
+// canonical layout: 8-row x 16-byte core matrices; element (r, k) of a chunk
+// at byte (r / 8) * SBO + (k / 4) * 128 + (r % 8) * 16 + (k % 4) * 4, with
+// SBO = KC / 4 * 128 (the 8-row groups follow each other) and the K-direction
+// core-matrix stride (LBO) 128 bytes.  One MMA consumes K = 8 (two core
+// matrices), so its descriptor start advances by 256 bytes per K step.
+//
+// Precision: every FP32 operand x is split as x = hi + lo with hi = tf32(x)
+// and lo = tf32(x - hi); the product uses hi*hi + hi*lo + lo*hi (three MMAs
+// accumulated in FP32, "3xTF32"), which keeps about FP32 accuracy.
+#pragma once
+#include <stdint.h>
+#include "blr_internal.h"
+
+#define TC_KC 32                        // K elements per staged chunk
+#define TC_SBO (TC_KC / 4 * 128)        // bytes between 8-row groups of a chunk
+#define TC_M 128                        // rows per MMA (cta_group::1)
+
+namespace {
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ unsigned long long tc_gtimer() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// ---- TMEM ------------------------------------------------------------------
+// Called by one whole warp.  Writes the TMEM base address to *dst (shared).
+__device__ __forceinline__ void tmem_alloc(uint32_t* dst, uint32_t ncols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(dst)),
+               "r"(ncols)
+               : "memory");
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+// Generic-proxy shared-memory writes become visible to the tensor core.
+__device__ __forceinline__ void fence_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+// ---- mbarrier --------------------------------------------------------------
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+// Waits until the phase with the given parity has completed; gives up after
+// limit_ns and returns false (the caller flags a timeout, never traps).
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, unsigned long long limit_ns) {
+  const uint32_t a = smem_u32(bar);
+  const unsigned long long t0 = tc_gtimer();
+  while (true) {
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(a), "r"(parity)
+        : "memory");
+    if (done) return true;
+    if (tc_gtimer() - t0 > limit_ns) return false;
+  }
+}
+
+// ---- descriptors -------------------------------------------------------------
+// Shared-memory matrix descriptor, no swizzle, K-major canonical layout.
+__device__ __forceinline__ uint64_t tc_desc(uint32_t saddr) {
+  uint64_t d = (uint64_t)((saddr & 0x3FFFFu) >> 4);
+  d |= (uint64_t)(128u >> 4) << 16;          // K-direction core-matrix stride
+  d |= (uint64_t)(TC_SBO >> 4) << 32;        // 8-row group stride
+  d |= (uint64_t)1 << 46;                    // descriptor version for tcgen05
+  return d;                                  // base offset 0, no swizzle
+}
+
+// Instruction descriptor: kind::tf32, D = F32, A = B = TF32, both K-major,
+// M x N (M = 128, N a multiple of 16 up to 256).
+__device__ __forceinline__ uint32_t tc_idesc(int m, int n) {
+  return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(m >> 4) << 24);
+}
+
+// One thread issues D (+)= A B^T for one K = 8 step.
+__device__ __forceinline__ void tc_mma(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+      "l"(a), "l"(b), "r"(idesc), "r"(acc)
+      : "memory");
+}
+
+// The mbarrier receives one arrival when every MMA issued so far by this
+// thread has completed.
+__device__ __forceinline__ void tc_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                   smem_u32(bar))
+               : "memory");
+}
+
+// 32 lanes x 16 consecutive 32-bit columns: thread t of the warp receives
+// lane (taddr.lane + t), columns taddr.col .. +15.
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr)
+      : "memory");
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 16; i++) v[i] = __uint_as_float(r[i]);
+}
+
+// ---- operand staging ----------------------------------------------------------
+__device__ __forceinline__ float tf32_hi(float x) {
+  uint32_t u;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(u) : "f"(x));
+  return __uint_as_float(u);
+}
+
+template <class G>
+__device__ __forceinline__ G tc_ld(const G* p) { return __ldcg(p); }
+
+// Stages rows [0, rows) x K columns [k0, k0 + TC_KC) of a strided global
+// operand (element (r, k) at p[r * sr + k * sc], element type G) into a
+// chunk pair (hi, lo) in the canonical layout above; rows >= nrow and
+// columns >= kmax are zero.  rows must be a multiple of 8.
+template <class G>
+__device__ void tc_stage(float* hi, float* lo, const G* p, long long sr, long long sc, int rows, int nrow,
+                         int k0, int kmax) {
+  const int groups = rows * (TC_KC / 4);       // (row, 4-column group) pairs
+  if (sc == 1) {
+    // K contiguous in global: eight consecutive threads take eight rows of
+    // one 4-column group (a 128-byte run of shared memory, no conflicts).
+    for (int e = threadIdx.x; e < groups; e += BLR_NT) {
+      const int r8 = e & 7, kq = (e >> 3) % (TC_KC / 4), rg = e / (8 * (TC_KC / 4));
+      const int r = rg * 8 + r8, k = k0 + kq * 4;
+      float h[4], l[4];
+#pragma unroll
+      for (int i = 0; i < 4; i++) {
+        G v = G(0);
+        if (r < nrow && k + i < kmax) v = tc_ld(p + (long long)r * sr + (k + i));
+        const float f = (float)v;
+        h[i] = tf32_hi(f);
+        l[i] = tf32_hi((float)(v - (G)h[i]));
+      }
+      const int off = (rg * TC_SBO + kq * 128 + r8 * 16) >> 2;
+      *reinterpret_cast<float4*>(hi + off) = make_float4(h[0], h[1], h[2], h[3]);
+      *reinterpret_cast<float4*>(lo + off) = make_float4(l[0], l[1], l[2], l[3]);
+    }
+  } else {
+    // rows contiguous in global: consecutive threads take consecutive rows.
+    for (int e = threadIdx.x; e < groups; e += BLR_NT) {
+      const int r = e % rows, kq = e / rows;
+      const int k = k0 + kq * 4;
+      float h[4], l[4];
+#pragma unroll
+      for (int i = 0; i < 4; i++) {
+        G v = G(0);
+        if (r < nrow && k + i < kmax) v = tc_ld(p + (long long)r * sr + (long long)(k + i) * sc);
+        const float f = (float)v;
+        h[i] = tf32_hi(f);
+        l[i] = tf32_hi((float)(v - (G)h[i]));
+      }
+      const int off = ((r >> 3) * TC_SBO + kq * 128 + (r & 7) * 16) >> 2;
+      *reinterpret_cast<float4*>(hi + off) = make_float4(h[0], h[1], h[2], h[3]);
+      *reinterpret_cast<float4*>(lo + off) = make_float4(l[0], l[1], l[2], l[3]);
+    }
+  }
+}
+
+// Shared state of the tensor-core GEMM inside a CTA.
+struct TcCtx {
+  uint32_t tmem;        // TMEM base (lane 0, first allocated column)
+  uint64_t* bar;        // two mbarriers (one per staging buffer)
+  uint32_t* phase;      // their next parity bits (shared, 2 words)
+  float* buf;           // staging: 2 buffers x (A hi, A lo, B hi, B lo)
+  int bcap;             // row capacity of the B staging (<= 256)
+  int* status;
+  unsigned long long limit_ns;
+};
+
+__device__ __forceinline__ size_t tc_chunk_floats(int rows) { return (size_t)rows * TC_KC; }
+
+// D (TC_M x ncol, TMEM columns [col0, col0 + ncol)) = sum over K of
+// A[r, k] * B[n, k], for r < TC_M (rows >= mrow read as zero), n < ncol
+// (a multiple of 16, <= t.bcap; rows >= nrow of B read as zero), k < K.  3xTF32 products, FP32
+// accumulation.  Called by all threads; returns with the result complete in
+// TMEM (and false if a wait ran out, after flagging ST_TIMEOUT).
+template <class GA, class GB>
+__device__ bool tc_gemm_tile(TcCtx& t, uint32_t col0, const GA* A, long long sar, long long sak, int mrow,
+                             const GB* B, long long sbn, long long sbk, int nrow, int ncol, int K) {
+  const size_t fa = tc_chunk_floats(TC_M), fb = tc_chunk_floats(t.bcap);
+  const size_t per = 2 * fa + 2 * fb;
+  const uint32_t idesc = tc_idesc(TC_M, ncol);
+  const int nchunk = (K + TC_KC - 1) / TC_KC;
+  bool ok = true;
+  for (int c = 0; c < nchunk; c++) {
+    const int s = c & 1;
+    float* ah = t.buf + s * per;
+    float* al = ah + fa;
+    float* bh = al + fa;
+    float* bl = bh + fb;
+    // the buffer was last read by the MMAs of chunk c - 2
+    if (c >= 2) {
+      if (!mbar_wait(t.bar + s, t.phase[s], t.limit_ns)) ok = false;
+      __syncthreads();
+      if (threadIdx.x == 0) t.phase[s] ^= 1u;
+    }
+    tc_stage(ah, al, A, sar, sak, TC_M, mrow, c * TC_KC, K);
+    tc_stage(bh, bl, B, sbn, sbk, ncol, nrow, c * TC_KC, K);
+    fence_async_smem();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      tc_fence_after();
+      const uint32_t a0 = smem_u32(ah), a1 = smem_u32(al), b0 = smem_u32(bh), b1 = smem_u32(bl);
+#pragma unroll
+      for (int ks = 0; ks < TC_KC / 8; ks++) {
+        const uint32_t o = ks * 256;
+        const uint32_t acc = (c > 0 || ks > 0) ? 1u : 0u;
+        tc_mma(t.tmem + col0, tc_desc(a1 + o), tc_desc(b0 + o), idesc, acc);
+        tc_mma(t.tmem + col0, tc_desc(a0 + o), tc_desc(b1 + o), idesc, 1u);
+        tc_mma(t.tmem + col0, tc_desc(a0 + o), tc_desc(b0 + o), idesc, 1u);
+      }
+      tc_commit(t.bar + s);
+    }
+  }
+  // drain: wait for the last one or two chunks
+  for (int c = (nchunk >= 2 ? nchunk - 2 : 0); c < nchunk; c++) {
+    const int s = c & 1;
+    if (!mbar_wait(t.bar + s, t.phase[s], t.limit_ns)) ok = false;
+    __syncthreads();
+    if (threadIdx.x == 0) t.phase[s] ^= 1u;
+  }
+  __syncthreads();
+  tc_fence_after();
+  if (!ok && threadIdx.x == 0) atomicOr(t.status, ST_TIMEOUT);
+  return ok;
+}
+
+// Reads the TC_M x ncol accumulator at TMEM columns [col0, col0 + ncol)
+// and calls f(row, col, value) for every element (each once).  Warps w and
+// w + 4 share TMEM lanes 32 (w % 4) .. + 31 and split the columns.
+template <class F>
+__device__ void tc_epilogue(const TcCtx& t, uint32_t col0, int ncol, F f) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int quarter = warp & 3, half = warp >> 2;
+  const int row = quarter * 32 + lane;
+  const int nblk = ncol / 16;
+  for (int cb = half; cb < nblk; cb += 2) {
+    float v[16];
+    tmem_ld16(t.tmem + ((uint32_t)(quarter * 32) << 16) + col0 + cb * 16, v);
+#pragma unroll
+    for (int i = 0; i < 16; i++) f(row, cb * 16 + i, v[i]);
+  }
+  tc_fence_before();
+  __syncthreads();
+}
+
+}  // namespace
