@@ -10,6 +10,7 @@
 #pragma once
 #include "blr_device.cuh"
 #include "blr_dag.h"
+#include "blr_tc.cuh"
 
 namespace {
 
@@ -22,6 +23,7 @@ struct TaskEnv {
   double* slab;
   size_t used;
   bool overflow;
+  TcCtx* tc;          // tensor-core state (mixed path), else nullptr
   __device__ double* alloc(size_t n) {
     const size_t nn = (n + 31) & ~(size_t)31;   // 256-byte granules
     if (used + nn > P->slab) {
@@ -434,6 +436,176 @@ __device__ void tpmqrt_core(TaskEnv& env, S* Yt, int rY, const S* Tik, S* Rt, in
   recompress_side(env, Uf, b, H, TH, H0, s, At, nA, c);
 }
 
+
+// ---------------------------------------------------------------------------
+// Mixed path on the tensor cores: the dense trapezoidal update.
+// ---------------------------------------------------------------------------
+
+// D (b x b, FP64, ld b) = U V^T for a low-rank tile (U, V: b x r in tile
+// layout) on the tensor cores.
+__device__ void tc_densify(TaskEnv& env, const double* Tl, int r, double* D, Ctx& c) {
+  TcCtx& tc = *env.tc;
+  const int b = env.P->b, cap = env.P->cap;
+  if (r == 0) {
+    zero_mat(D, b, b, b);
+    __syncthreads();
+    return;
+  }
+  const double* U = Tl;
+  const double* V = Tl + (size_t)b * cap;
+  for (int r0 = 0; r0 < b; r0 += TC_M) {
+    const int mrow = min(TC_M, b - r0);
+    for (int n0 = 0; n0 < b; n0 += 256) {
+      const int nn = min(256, b - n0), nn16 = (nn + 15) & ~15;
+      tc_gemm_tile(tc, n0, U + r0, 1, b, mrow, V + n0, 1, b, nn, nn16, r);
+    }
+    for (int n0 = 0; n0 < b; n0 += 256) {
+      const int nn = min(256, b - n0), nn16 = (nn + 15) & ~15;
+      tc_epilogue(tc, n0, nn16, [&](int rr, int cc, float v) {
+        if (rr < mrow && cc < nn) D[(r0 + rr) + (size_t)(n0 + cc) * b] = (double)v;
+      });
+    }
+  }
+  c.fma += (double)b * b * r;
+}
+
+// T of a group of wg <= 128 consecutive reflectors (Eq. 3's compact WY form
+// of their product) from the stored inner 32-reflector blocks and the Gram
+// matrix G = Y_g^T Y_g of their tails (the identity parts are mutually
+// orthogonal): T(0:J, J) = -T(0:J, 0:J) G(0:J, J) T_J, block column by
+// block column.  Gs, Ts (ld 128) and X (ld 128, 32 columns) are shared
+// memory; Ts receives the wg x wg upper triangle (zeros elsewhere).
+__device__ void tc_group_t(const double* Tblk, int wg, const float* Gs, float* Ts, float* X, Ctx& c) {
+  for (int e = threadIdx.x; e < 128 * 128; e += BLR_NT) {
+    const int a = e & 127, l = e >> 7;
+    float v = 0.f;
+    if (a < wg && l < wg && (a >> 5) == (l >> 5) && a <= l) v = (float)ldg(Tblk + (size_t)l * BLR_NB + (a & 31));
+    Ts[e] = v;
+  }
+  __syncthreads();
+  for (int J = 1; J * BLR_NB < wg; J++) {
+    const int top = J * BLR_NB;
+    for (int e = threadIdx.x; e < top * BLR_NB; e += BLR_NT) {
+      const int a = e % top, m = e / top;
+      float s = 0.f;
+      for (int l = 0; l <= m; l++) s += Gs[a + (top + l) * 128] * Ts[(top + l) + (top + m) * 128];
+      X[a + m * 128] = s;
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < top * BLR_NB; e += BLR_NT) {
+      const int a = e % top, m = e / top;
+      float s = 0.f;
+      for (int l = a; l < top; l++) s += Ts[a + l * 128] * X[l + m * 128];
+      Ts[a + (top + m) * 128] = -s;
+    }
+    __syncthreads();
+    c.fma += (double)top * BLR_NB * BLR_NB / 2 + (double)top * top * BLR_NB / 2;
+  }
+}
+
+// [Ct (b x nc, ld ldt); Cb (b x nc, ld ldb)] <- Q^T [Ct; Cb] for the dense
+// reflector block of a TSQRT, Q = I - [I; Y] T [I; Y]^T with Y b x b dense
+// (Section 3.4.4, Eq. 21), in groups of 128 reflectors:
+//   Z = Ct(g rows) + Y_g^T Cb;  W = T_g^T Z;  Ct(g rows) -= W;  Cb -= Y_g W.
+// Products on the tensor cores (3xTF32, FP32 accumulation); the tiles stay
+// FP64 and receive FP64 updates.
+__device__ void tc_apply_ts_dense(TaskEnv& env, const double* Y, const double* Tik, double* Ct, long long ldt,
+                                  double* Cb, long long ldb, int nc, Ctx& c) {
+  TcCtx& tc = *env.tc;
+  const int b = env.P->b;
+  float* Tg = (float*)env.alloc(128 * 128 / 2);          // global copy of T_g (A operand of W)
+  float* Zs = (float*)env.alloc((size_t)128 * nc / 2);   // Z, then W (ld 128)
+  float* Gsm = tc.buf;                                   // staging area, idle between products
+  float* Tsm = tc.buf + 128 * 128;
+  float* Xsm = tc.buf + 2 * 128 * 128;
+  for (int c0 = 0; c0 < b; c0 += 128) {
+    const int wg = min(128, b - c0);
+    const double* Yg = Y + (size_t)c0 * b;
+    // G = Y_g^T Y_g
+    tc_gemm_tile(tc, 0, Yg, b, 1, wg, Yg, b, 1, wg, wg, b);
+    tc_epilogue(tc, 0, wg, [&](int r, int col, float v) { Gsm[r + col * 128] = v; });
+    c.fma += (double)wg * wg * b / 2;
+    tc_group_t(Tik + (size_t)c0 * BLR_NB, wg, Gsm, Tsm, Xsm, c);
+    for (int e = threadIdx.x; e < 128 * 128; e += BLR_NT) Tg[e] = Tsm[e];
+    __syncthreads();
+    // Z = Ct(c0 : c0 + wg, :) + Y_g^T Cb
+    for (int n0 = 0; n0 < nc; n0 += 256) {
+      const int nn = min(256, nc - n0), nn16 = (nn + 15) & ~15;
+      tc_gemm_tile(tc, n0, Yg, b, 1, wg, Cb + (size_t)n0 * ldb, ldb, 1, nn, nn16, b);
+    }
+    for (int n0 = 0; n0 < nc; n0 += 256) {
+      const int nn = min(256, nc - n0), nn16 = (nn + 15) & ~15;
+      tc_epilogue(tc, n0, nn16, [&](int r, int col, float v) {
+        if (r < wg && col < nn) {
+          const size_t n = n0 + col;
+          Zs[r + n * 128] = v + (float)ldg(Ct + (c0 + r) + n * ldt);
+        }
+      });
+    }
+    // W = T_g^T Z; Ct(c0 : c0 + wg, :) -= W
+    for (int n0 = 0; n0 < nc; n0 += 256) {
+      const int nn = min(256, nc - n0), nn16 = (nn + 15) & ~15;
+      tc_gemm_tile(tc, n0, (const float*)Tg, 128, 1, wg, (const float*)Zs + (size_t)n0 * 128, 128, 1, nn, nn16, wg);
+    }
+    for (int n0 = 0; n0 < nc; n0 += 256) {
+      const int nn = min(256, nc - n0), nn16 = (nn + 15) & ~15;
+      tc_epilogue(tc, n0, nn16, [&](int r, int col, float v) {
+        if (r < wg && col < nn) {
+          const size_t n = n0 + col;
+          double* p = Ct + (c0 + r) + n * ldt;
+          *p = ldg(p) - (double)v;
+          Zs[r + n * 128] = v;
+        }
+      });
+    }
+    // Cb -= Y_g W
+    for (int r0 = 0; r0 < b; r0 += TC_M) {
+      const int mrow = min(TC_M, b - r0);
+      for (int n0 = 0; n0 < nc; n0 += 256) {
+        const int nn = min(256, nc - n0), nn16 = (nn + 15) & ~15;
+        tc_gemm_tile(tc, n0, Yg + r0, 1, b, mrow, (const float*)Zs + (size_t)n0 * 128, 128, 1, nn, nn16, wg);
+      }
+      for (int n0 = 0; n0 < nc; n0 += 256) {
+        const int nn = min(256, nc - n0), nn16 = (nn + 15) & ~15;
+        tc_epilogue(tc, n0, nn16, [&](int r, int col, float v) {
+          if (r < mrow && col < nn) {
+            double* p = Cb + (r0 + r) + (size_t)(n0 + col) * ldb;
+            *p = ldg(p) - (double)v;
+          }
+        });
+      }
+    }
+    c.fma += (double)wg * nc * b + (double)wg * nc * wg / 2 + (double)b * nc * wg;
+  }
+}
+
+// TPMQRT(i,j,k) with a dense reflector block and a dense R_kj or A_ij, on
+// the tensor cores: a low-rank operand is densified (it becomes dense, as
+// OP1 of Section 3.1 makes it), then the block reflector is applied.
+__device__ void tpmqrt_tc_dense(TaskEnv& env, const double* Yt, const double* Tik, double* Rt, int rR, double* At,
+                                int rA, int* nR, int* nA, Ctx& c) {
+  const int b = env.P->b;
+  double* Rd = Rt;
+  double* Ad = At;
+  if (rR >= 0) {
+    Rd = env.alloc((size_t)b * b);
+    tc_densify(env, Rt, rR, Rd, c);
+  }
+  if (rA >= 0) {
+    Ad = env.alloc((size_t)b * b);
+    tc_densify(env, At, rA, Ad, c);
+  }
+  tc_apply_ts_dense(env, Yt, Tik, Rd, b, Ad, b, b, c);
+  if (rR >= 0) copy_mat(Rt, b, Rd, b, b, b);
+  if (rA >= 0) copy_mat(At, b, Ad, b, b, b);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    if (rR >= 0) *nR = -1;
+    if (rA >= 0) *nA = -1;
+  }
+  __syncthreads();
+}
+
 // Copies the live part of a tile (rank r: U and V columns; -1: dense) between
 // storage types.
 template <class D, class Src>
@@ -462,6 +634,10 @@ __device__ void task_tpmqrt(TaskEnv& env, int i, int j, int k, Ctx& c) {
     return;
   }
   if (rY == 0) return;
+  if (rY < 0 && (rR < 0 || rA < 0) && env.tc) {
+    tpmqrt_tc_dense(env, Yt, Tik, Rt, rR, At, rA, rank_ptr(P, k, j), rank_ptr(P, i, j), c);
+    return;
+  }
   // mixed: FP32 copies of the operands, FP32 arithmetic, results back to FP64
   float* Yf = (float*)env.alloc((size_t)b * b / 2);
   float* Tf = (float*)env.alloc((size_t)BLR_NB * b / 2);
@@ -554,7 +730,34 @@ __global__ void __launch_bounds__(BLR_NT, 1) k_factor(SchedParams P) {
   c.s = sm_carve(smem);
   c.status = P.status;
   DagShape d{P.p, P.q, P.off_larfb, P.off_tsqrt, P.off_tpmqrt};
-  TaskEnv env{&P, P.scratch + (size_t)blockIdx.x * P.slab, 0, false};
+  TaskEnv env{&P, P.scratch + (size_t)blockIdx.x * P.slab, 0, false, nullptr};
+  constexpr bool kTensor = std::is_same<S, float>::value;
+  static_assert(BLR_SMEM_BYTES >= TC_STAGE_BYTES && TC_STAGE_BYTES >= 3 * 128 * 128 * 4, "staging area");
+  __shared__ uint64_t tc_bars[2];
+  __shared__ uint32_t tc_phase[2];
+  __shared__ uint32_t tc_tmem;
+  TcCtx tcx;
+  if (kTensor) {
+    // the mixed path's tensor-core state: all 512 TMEM columns (one CTA per
+    // SM), two mbarriers for the double-buffered operand staging
+    if (threadIdx.x < 32) tmem_alloc(&tc_tmem, 512);
+    if (threadIdx.x == 0) {
+      mbar_init(&tc_bars[0], 1);
+      mbar_init(&tc_bars[1], 1);
+      tc_phase[0] = tc_phase[1] = 0;
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    tcx.tmem = tc_tmem;
+    tcx.bar = tc_bars;
+    tcx.phase = tc_phase;
+    tcx.buf = reinterpret_cast<float*>(smem);
+    tcx.bcap = 256;
+    tcx.status = P.status;
+    tcx.limit_ns = (unsigned long long)P.watchdog_ns;
+    env.tc = &tcx;
+  }
   while (true) {
     if (threadIdx.x == 0) task_sh = q_pop(P);
     __syncthreads();
@@ -606,6 +809,11 @@ __global__ void __launch_bounds__(BLR_NT, 1) k_factor(SchedParams P) {
       __threadfence();
       atomicAdd(P.done, 1);
     }
+  }
+  if (kTensor) {
+    tc_fence_before();
+    __syncthreads();
+    if (threadIdx.x < 32) tmem_dealloc(tc_tmem, 512);
   }
 }
 

@@ -21,6 +21,7 @@
 #define TC_KC 32                        // K elements per staged chunk
 #define TC_SBO (TC_KC / 4 * 128)        // bytes between 8-row groups of a chunk
 #define TC_M 128                        // rows per MMA (cta_group::1)
+#define TC_STAGE_BYTES (2 * (2 * TC_M * TC_KC + 2 * 256 * TC_KC) * 4)   // double-buffered staging, N <= 256
 
 namespace {
 
