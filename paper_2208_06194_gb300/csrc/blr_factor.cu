@@ -51,8 +51,22 @@ int blr_launch_factor(blr_factor* f, const blr_opts* o, cudaStream_t st) {
     blr_set_error("blr_qr: out of device memory (scratch %zu MB)", sizeof(double) * slab * ctas >> 20);
     return BLR_ERR_OOM;
   }
+  // mixed path: tensor-core operands of every dense reflector block, one
+  // slot per (i,k) with i >= k (the T layout), 6 x Rp x b floats each; if the
+  // device cannot hold them the updates stage their operands themselves
+  float* prep = nullptr;
+  const int prep_rp = (b + 127) / 128 * 128;
+  if (o->precision == BLR_PREC_MIXED) {
+    const size_t pbytes = (size_t)f->nt * 6 * prep_rp * b * sizeof(float);
+    if (cudaMalloc(&prep, pbytes) != cudaSuccess) {
+      prep = nullptr;
+      cudaGetLastError();
+    }
+  }
   int rc = BLR_OK;
   SchedParams P{};
+  P.prep = prep;
+  P.prep_rp = prep_rp;
   P.p = p; P.q = q; P.b = b; P.cap = A.cap;
   P.dense_rank = (o->dense_rank > 0 && o->dense_rank <= A.cap) ? o->dense_rank : A.cap;
   P.precision = o->precision;
@@ -137,6 +151,7 @@ int blr_launch_factor(blr_factor* f, const blr_opts* o, cudaStream_t st) {
   if (e1) cudaEventDestroy(e1);
   cudaFree(scratch);
   cudaFree(base);
+  if (prep) cudaFree(prep);
   return rc;
 }
 

@@ -90,6 +90,8 @@ struct SchedParams {
   unsigned long long* nvar;      // 8 counters: updates per operand kind (4 Y dense + 2 R dense + A dense)
   unsigned long long* tvar;      // 8 counters: their summed durations (ns)
   double* fvar;                  // 8 counters: their counted flops
+  float* prep;                   // mixed path: per (i,k) slot, tensor-core operands of a dense Y~_ik, or NULL
+  int prep_rp;                   // rows of those operands (b rounded up to 128)
 };
 
 // host helpers (blr_api.cu)

@@ -24,6 +24,9 @@ struct TaskEnv {
   size_t used;
   bool overflow;
   TcCtx* tc;          // tensor-core state (mixed path), else nullptr
+  const TcBulk* tq;   // its bulk-copy pipeline barriers
+  const DagShape* dag;
+  int skip_succ;      // a successor the task body has already released (-1: none)
   __device__ double* alloc(size_t n) {
     const size_t nn = (n + 31) & ~(size_t)31;   // 256-byte granules
     if (used + nn > P->slab) {
@@ -46,6 +49,23 @@ __device__ __forceinline__ double* t_ptr(const SchedParams& P, int i, int k) {
   return P.t + (size_t)(P.toff_dev[k] + (i - k)) * BLR_NB * P.b;
 }
 __device__ __forceinline__ int ld_rank(const int* p) { return __ldcg(p); }
+
+__device__ void q_push(const SchedParams& P, int qi, int task);
+
+// Thread 0: one dependency of task sid is satisfied; queue it when ready.
+__device__ void release_task(const SchedParams& P, const DagShape& d, int sid) {
+  if (atomicSub(P.deps + sid, 1) == 1) {
+    __threadfence();
+    int si, sj, sk;
+    const int st = dag_decode(d, sid, &si, &sj, &sk);
+    q_push(P, dag_queue(st, si, sj, sk), sid);
+  }
+}
+
+// Slot of the tensor-core operands prepared for the reflector block (i,k).
+__device__ __forceinline__ float* prep_ptr(const SchedParams& P, int i, int k) {
+  return P.prep + (size_t)(P.toff_dev[k] + (i - k)) * 6 * P.prep_rp * P.b;
+}
 
 // ---------------------------------------------------------------------------
 // TSQRT panel: Householder on [Rp (w x w upper, ld NB); Bp (ry x w, ld ldb)],
@@ -220,6 +240,187 @@ __device__ void task_larfb(TaskEnv& env, int k, int j, Ctx& c) {
   if (nc > 0) apply_q<S>(tile_ptr(P, k, k), b, b, b, t_ptr(P, k, k), C, b, nc, true, c);
 }
 
+
+// ---------------------------------------------------------------------------
+// Mixed path: tensor-core operands of a dense reflector block, prepared once
+// by TSQRT(i,k) for all the updates TPMQRT(i,j,k) that apply it.  The slot
+// holds, each as a pre-split (hi, lo) canonical operand of Rp x b:
+//   Yt: rows = reflectors a, K = tile rows   (Y^T, for Z = Y^T C)
+//   Yc: rows = tile rows, K = reflectors a   (Y, for C -= Y W)
+//   Tt: rows = reflectors a, K = reflectors  (T^T of the whole block, for W = T^T Z)
+// where T is the b x b upper triangular factor of the compact WY form of all
+// b reflectors (Eq. 3), assembled from the stored 32-reflector blocks and the
+// Gram matrix G = Y^T Y of the tails (the identity parts are orthogonal):
+// T(0:J, J) = -T(0:J, 0:J) G(0:J, J) T_J, one 32-column block J at a time.
+// ---------------------------------------------------------------------------
+__device__ void tsqrt_prep(TaskEnv& env, int i, int k, Ctx& c) {
+  const SchedParams& P = *env.P;
+  TcCtx& tc = *env.tc;
+  const int b = P.b, Rp = P.prep_rp;
+  const size_t op = (size_t)Rp * b;
+  float* slot = prep_ptr(P, i, k);
+  float *yt_h = slot, *yt_l = slot + op, *yc_h = slot + 2 * op, *yc_l = slot + 3 * op, *tt_h = slot + 4 * op,
+        *tt_l = slot + 5 * op;
+  const double* Y = tile_ptr(P, i, k);
+  const double* Tk = t_ptr(P, i, k);
+  tc_canon(yt_h, yt_l, Rp, b, Y, b, 1, b, b);      // (a, r) = Y[r + a b]
+  tc_canon(yc_h, yc_l, Rp, b, Y, 1, b, b, b);      // (r, a) = Y[r + a b]
+  fence_async_global();
+  __syncthreads();
+  // G = Y^T Y (FP32, ld b, upper block triangle)
+  float* G = (float*)env.alloc((size_t)b * b / 2);
+  float* T = (float*)env.alloc((size_t)b * b / 2);
+  const size_t cs = (size_t)Rp * TC_KC;
+  for (int m0 = 0; m0 < b; m0 += TC_M) {
+    for (int n0 = 0; n0 < b; n0 += 256) {
+      if (n0 + 256 <= m0) continue;       // strictly below the diagonal: not needed
+      const int nn = min(256, b - n0), nn16 = (nn + 15) & ~15;
+      tc_gemm_bulk(tc, *env.tq, n0, yt_h + (size_t)m0 * TC_KC, yt_l + (size_t)m0 * TC_KC, cs,
+                   yt_h + (size_t)n0 * TC_KC, yt_l + (size_t)n0 * TC_KC, cs, nn16, b / TC_KC);
+    }
+    for (int n0 = 0; n0 < b; n0 += 256) {
+      if (n0 + 256 <= m0) continue;
+      const int nn = min(256, b - n0), nn16 = (nn + 15) & ~15;
+      tc_epilogue(tc, n0, nn16, [&](int r, int col, float v) {
+        if (m0 + r < b && col < nn) G[(m0 + r) + (size_t)(n0 + col) * b] = v;
+      });
+    }
+  }
+  c.fma += (double)b * b * b / 2;
+  // T, block column by block column (X = G(0:J, J) T_J in shared memory)
+  for (int e = threadIdx.x; e < b * b; e += BLR_NT) {
+    const int a = e % b, l = e / b;
+    T[e] = ((a >> 5) == (l >> 5) && a <= l) ? (float)ldg(Tk + (size_t)l * BLR_NB + (a & 31)) : 0.f;
+  }
+  __syncthreads();
+  float* X = tc.buf;                      // top x 32, ld b (the staging area is idle here)
+  for (int J = 1; J * BLR_NB < b; J++) {
+    const int top = J * BLR_NB;
+    for (int e = threadIdx.x; e < top * BLR_NB; e += BLR_NT) {
+      const int a = e % top, m = e / top;
+      float s = 0.f;
+      for (int l = 0; l <= m; l++) s += __ldcg(G + a + (size_t)(top + l) * b) * __ldcg(T + (top + l) + (size_t)(top + m) * b);
+      X[a + m * b] = s;
+    }
+    __syncthreads();
+    // T(0:top, J) = -T(0:top, 0:top) X: thread = (row a, 8 columns)
+    for (int e = threadIdx.x; e < top * 4; e += BLR_NT) {
+      const int a = e % top, m0 = (e / top) * 8;
+      float s[8];
+#pragma unroll
+      for (int u = 0; u < 8; u++) s[u] = 0.f;
+      for (int l = a; l < top; l++) {
+        const float t = __ldcg(T + a + (size_t)l * b);
+#pragma unroll
+        for (int u = 0; u < 8; u++) s[u] += t * X[l + (m0 + u) * b];
+      }
+#pragma unroll
+      for (int u = 0; u < 8; u++) T[a + (size_t)(top + m0 + u) * b] = -s[u];
+    }
+    __syncthreads();
+    c.fma += (double)top * BLR_NB * BLR_NB / 2 + (double)top * top * BLR_NB / 2;
+  }
+  tc_canon(tt_h, tt_l, Rp, b, (const float*)T, b, 1, b, b);   // (a, k) = T(k, a) = T[k + a b]
+  fence_async_global();
+  __threadfence();
+  __syncthreads();
+}
+
+// [Ct; Cb] <- Q^T [Ct; Cb] (Ct, Cb: b x b FP64, ld b) for a dense reflector
+// block with prepared operands: Z = Ct + Y^T Cb, W = T^T Z, Ct -= W,
+// Cb -= Y W, all b reflectors at once (three b x b x b products, the second
+// one triangular), on the tensor cores with bulk-copied operands.
+__device__ void tc_apply_prepared(TaskEnv& env, const float* slot, double* Ct, double* Cb, Ctx& c) {
+  const SchedParams& P = *env.P;
+  TcCtx& tc = *env.tc;
+  const TcBulk& q = *env.tq;
+  const int b = P.b, Rp = P.prep_rp;
+  const size_t op = (size_t)Rp * b, cs = (size_t)Rp * TC_KC;
+  const float *yt_h = slot, *yt_l = slot + op, *yc_h = slot + 2 * op, *yc_l = slot + 3 * op, *tt_h = slot + 4 * op,
+              *tt_l = slot + 5 * op;
+  float* cc_h = (float*)env.alloc(op / 2);    // Cb as an operand (rows = columns n), later W
+  float* cc_l = (float*)env.alloc(op / 2);
+  float* zc_h = (float*)env.alloc(op / 2);    // Z as an operand (rows = columns n, K = reflectors)
+  float* zc_l = (float*)env.alloc(op / 2);
+  tc_canon(cc_h, cc_l, Rp, b, (const double*)Cb, b, 1, b, b);    // (n, r) = Cb[r + n b]
+  fence_async_global();
+  __syncthreads();
+  const int nchunk = b / TC_KC;
+  // Z = Ct + Y^T Cb
+  for (int m0 = 0; m0 < b; m0 += TC_M) {
+    for (int n0 = 0; n0 < b; n0 += 256) {
+      const int nn = min(256, b - n0), nn16 = (nn + 15) & ~15;
+      tc_gemm_bulk(tc, q, n0, yt_h + (size_t)m0 * TC_KC, yt_l + (size_t)m0 * TC_KC, cs, cc_h + (size_t)n0 * TC_KC,
+                   cc_l + (size_t)n0 * TC_KC, cs, nn16, nchunk);
+    }
+    for (int n0 = 0; n0 < b; n0 += 256) {
+      const int nn = min(256, b - n0), nn16 = (nn + 15) & ~15;
+      tc_epilogue16(tc, n0, nn16, [&](int r, int col, const float* v) {
+        const int a = m0 + r;
+        if (a >= b) return;
+        double ct[16];
+#pragma unroll
+        for (int u = 0; u < 16; u++) ct[u] = (col + u < nn) ? ldg(Ct + a + (size_t)(n0 + col + u) * b) : 0.0;
+#pragma unroll
+        for (int u = 0; u < 16; u++)
+          if (col + u < nn) tc_canon_put(zc_h, zc_l, Rp, n0 + col + u, a, v[u] + (float)ct[u]);
+      });
+    }
+  }
+  fence_async_global();
+  __syncthreads();
+  // W = T^T Z (T^T lower triangular: rows m0.. need K < m0 + 128); Ct -= W
+  for (int m0 = 0; m0 < b; m0 += TC_M) {
+    const int kch = min(b, m0 + TC_M) / TC_KC;
+    for (int n0 = 0; n0 < b; n0 += 256) {
+      const int nn = min(256, b - n0), nn16 = (nn + 15) & ~15;
+      tc_gemm_bulk(tc, q, n0, tt_h + (size_t)m0 * TC_KC, tt_l + (size_t)m0 * TC_KC, cs, zc_h + (size_t)n0 * TC_KC,
+                   zc_l + (size_t)n0 * TC_KC, cs, nn16, kch);
+    }
+    for (int n0 = 0; n0 < b; n0 += 256) {
+      const int nn = min(256, b - n0), nn16 = (nn + 15) & ~15;
+      tc_epilogue16(tc, n0, nn16, [&](int r, int col, const float* v) {
+        const int a = m0 + r;
+        if (a >= b) return;
+        double ct[16];
+#pragma unroll
+        for (int u = 0; u < 16; u++) ct[u] = (col + u < nn) ? ldg(Ct + a + (size_t)(n0 + col + u) * b) : 0.0;
+#pragma unroll
+        for (int u = 0; u < 16; u++) {
+          if (col + u < nn) {
+            Ct[a + (size_t)(n0 + col + u) * b] = ct[u] - (double)v[u];
+            tc_canon_put(cc_h, cc_l, Rp, n0 + col + u, a, v[u]);    // W as an operand (rows = n, K = a)
+          }
+        }
+      });
+    }
+  }
+  fence_async_global();
+  __syncthreads();
+  // Cb -= Y W
+  for (int m0 = 0; m0 < b; m0 += TC_M) {
+    for (int n0 = 0; n0 < b; n0 += 256) {
+      const int nn = min(256, b - n0), nn16 = (nn + 15) & ~15;
+      tc_gemm_bulk(tc, q, n0, yc_h + (size_t)m0 * TC_KC, yc_l + (size_t)m0 * TC_KC, cs, cc_h + (size_t)n0 * TC_KC,
+                   cc_l + (size_t)n0 * TC_KC, cs, nn16, nchunk);
+    }
+    for (int n0 = 0; n0 < b; n0 += 256) {
+      const int nn = min(256, b - n0), nn16 = (nn + 15) & ~15;
+      tc_epilogue16(tc, n0, nn16, [&](int r, int col, const float* v) {
+        const int rr = m0 + r;
+        if (rr >= b) return;
+        double cb[16];
+#pragma unroll
+        for (int u = 0; u < 16; u++) cb[u] = (col + u < nn) ? ldg(Cb + rr + (size_t)(n0 + col + u) * b) : 0.0;
+#pragma unroll
+        for (int u = 0; u < 16; u++)
+          if (col + u < nn) Cb[rr + (size_t)(n0 + col + u) * b] = cb[u] - (double)v[u];
+      });
+    }
+  }
+  c.fma += 2.0 * b * b * b + (double)b * b * b / 2;
+}
+
 // TSQRT(i,k): QR([R_kk; A^V_ik]) with A^V = V^T (low-rank) or the dense tile
 // (Section 3.4.3, Eqs. 19-21); Y_ik overwrites A^V in place.  The panel
 // factorization is FP64; the update of the trailing columns runs in S.
@@ -269,6 +470,20 @@ __device__ void task_tsqrt(TaskEnv& env, int i, int k, Ctx& c) {
       }
     }
     __syncthreads();
+  }
+  if constexpr (std::is_same<S, float>::value) {
+    if (r < 0 && P.prep && env.tc) {
+      // release the next update QR of this column now (it needs only R_kk),
+      // then prepare the tensor-core operands for the updates TPMQRT(i,.,k)
+      __threadfence();
+      __syncthreads();
+      if (i + 1 < P.p && threadIdx.x == 0) {
+        const int sid = dag_id_tsqrt(*env.dag, i + 1, k);
+        release_task(P, *env.dag, sid);
+        env.skip_succ = sid;
+      }
+      tsqrt_prep(env, i, k, c);
+    }
   }
 }
 
@@ -582,8 +797,8 @@ __device__ void tc_apply_ts_dense(TaskEnv& env, const double* Y, const double* T
 // TPMQRT(i,j,k) with a dense reflector block and a dense R_kj or A_ij, on
 // the tensor cores: a low-rank operand is densified (it becomes dense, as
 // OP1 of Section 3.1 makes it), then the block reflector is applied.
-__device__ void tpmqrt_tc_dense(TaskEnv& env, const double* Yt, const double* Tik, double* Rt, int rR, double* At,
-                                int rA, int* nR, int* nA, Ctx& c) {
+__device__ void tpmqrt_tc_dense(TaskEnv& env, const double* Yt, const double* Tik, const float* prep, double* Rt,
+                                int rR, double* At, int rA, int* nR, int* nA, Ctx& c) {
   const int b = env.P->b;
   double* Rd = Rt;
   double* Ad = At;
@@ -595,7 +810,8 @@ __device__ void tpmqrt_tc_dense(TaskEnv& env, const double* Yt, const double* Ti
     Ad = env.alloc((size_t)b * b);
     tc_densify(env, At, rA, Ad, c);
   }
-  tc_apply_ts_dense(env, Yt, Tik, Rd, b, Ad, b, b, c);
+  if (prep) tc_apply_prepared(env, prep, Rd, Ad, c);
+  else tc_apply_ts_dense(env, Yt, Tik, Rd, b, Ad, b, b, c);
   if (rR >= 0) copy_mat(Rt, b, Rd, b, b, b);
   if (rA >= 0) copy_mat(At, b, Ad, b, b, b);
   __syncthreads();
@@ -635,7 +851,8 @@ __device__ void task_tpmqrt(TaskEnv& env, int i, int j, int k, Ctx& c) {
   }
   if (rY == 0) return;
   if (rY < 0 && (rR < 0 || rA < 0) && env.tc) {
-    tpmqrt_tc_dense(env, Yt, Tik, Rt, rR, At, rA, rank_ptr(P, k, j), rank_ptr(P, i, j), c);
+    tpmqrt_tc_dense(env, Yt, Tik, P.prep ? prep_ptr(P, i, k) : nullptr, Rt, rR, At, rA, rank_ptr(P, k, j),
+                    rank_ptr(P, i, j), c);
     return;
   }
   // mixed: FP32 copies of the operands, FP32 arithmetic, results back to FP64
@@ -730,13 +947,16 @@ __global__ void __launch_bounds__(BLR_NT, 1) k_factor(SchedParams P) {
   c.s = sm_carve(smem);
   c.status = P.status;
   DagShape d{P.p, P.q, P.off_larfb, P.off_tsqrt, P.off_tpmqrt};
-  TaskEnv env{&P, P.scratch + (size_t)blockIdx.x * P.slab, 0, false, nullptr};
+  TaskEnv env{&P, P.scratch + (size_t)blockIdx.x * P.slab, 0, false, nullptr, nullptr, &d, -1};
   constexpr bool kTensor = std::is_same<S, float>::value;
   static_assert(BLR_SMEM_BYTES >= TC_STAGE_BYTES && TC_STAGE_BYTES >= 3 * 128 * 128 * 4, "staging area");
   __shared__ uint64_t tc_bars[2];
   __shared__ uint32_t tc_phase[2];
   __shared__ uint32_t tc_tmem;
+  __shared__ uint64_t tq_full[2], tq_empty[2];
+  __shared__ uint32_t tq_ph[4];
   TcCtx tcx;
+  TcBulk tq{tq_full, tq_empty, tq_ph};
   if (kTensor) {
     // the mixed path's tensor-core state: all 512 TMEM columns (one CTA per
     // SM), two mbarriers for the double-buffered operand staging
@@ -745,6 +965,11 @@ __global__ void __launch_bounds__(BLR_NT, 1) k_factor(SchedParams P) {
       mbar_init(&tc_bars[0], 1);
       mbar_init(&tc_bars[1], 1);
       tc_phase[0] = tc_phase[1] = 0;
+      for (int s2 = 0; s2 < 2; s2++) {
+        mbar_init(&tq_full[s2], 1);
+        mbar_init(&tq_empty[s2], 1);
+      }
+      for (int s2 = 0; s2 < 4; s2++) tq_ph[s2] = 0;
     }
     tc_fence_before();
     __syncthreads();
@@ -757,6 +982,7 @@ __global__ void __launch_bounds__(BLR_NT, 1) k_factor(SchedParams P) {
     tcx.status = P.status;
     tcx.limit_ns = (unsigned long long)P.watchdog_ns;
     env.tc = &tcx;
+    env.tq = &tq;
   }
   while (true) {
     if (threadIdx.x == 0) task_sh = q_pop(P);
@@ -770,6 +996,7 @@ __global__ void __launch_bounds__(BLR_NT, 1) k_factor(SchedParams P) {
     c.fma = 0.0;
     env.used = 0;
     env.overflow = false;
+    env.skip_succ = -1;
     // operand kinds of an update, for the statistics: 4 (Y dense) + 2 (R dense) + (A dense)
     int variant = 0;
     if (type == TASK_TPMQRT && threadIdx.x == 0)
@@ -789,12 +1016,7 @@ __global__ void __launch_bounds__(BLR_NT, 1) k_factor(SchedParams P) {
     __syncthreads();
     if (threadIdx.x == 0 && type >= 0) {
       dag_for_each_successor(d, type, i, j, k, [&](int sid) {
-        if (atomicSub(P.deps + sid, 1) == 1) {
-          __threadfence();
-          int si, sj, sk;
-          const int st = dag_decode(d, sid, &si, &sj, &sk);
-          q_push(P, dag_queue(st, si, sj, sk), sid);
-        }
+        if (sid != env.skip_succ) release_task(P, d, sid);
       });
       const unsigned long long dt = gtimer() - t_start;
       atomicAdd(P.flops + type, 2.0 * c.fma);

@@ -58,6 +58,10 @@ __device__ __forceinline__ void tc_fence_after() {
 __device__ __forceinline__ void fence_async_smem() {
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
+// Generic-proxy global writes become visible to bulk copies (TMA reads).
+__device__ __forceinline__ void fence_async_global() {
+  asm volatile("fence.proxy.async.global;" ::: "memory");
+}
 
 // ---- mbarrier --------------------------------------------------------------
 __device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
@@ -137,6 +141,14 @@ __device__ __forceinline__ float tf32_hi(float x) {
   return __uint_as_float(u);
 }
 
+// x = hi + lo with hi = tf32(x) and lo = tf32(x - hi) (x - hi is exact in
+// FP32).  FP64 operands are first rounded to FP32: the dropped part is below
+// what the three products resolve, and the split then needs no FP64 work.
+__device__ __forceinline__ void tc_split(float x, float& hi, float& lo) {
+  hi = tf32_hi(x);
+  lo = tf32_hi(x - hi);
+}
+
 template <class G>
 __device__ __forceinline__ G tc_ld(const G* p) { return __ldcg(p); }
 
@@ -159,9 +171,7 @@ __device__ void tc_stage(float* hi, float* lo, const G* p, long long sr, long lo
       for (int i = 0; i < 4; i++) {
         G v = G(0);
         if (r < nrow && k + i < kmax) v = tc_ld(p + (long long)r * sr + (k + i));
-        const float f = (float)v;
-        h[i] = tf32_hi(f);
-        l[i] = tf32_hi((float)(v - (G)h[i]));
+        tc_split((float)v, h[i], l[i]);
       }
       const int off = (rg * TC_SBO + kq * 128 + r8 * 16) >> 2;
       *reinterpret_cast<float4*>(hi + off) = make_float4(h[0], h[1], h[2], h[3]);
@@ -177,9 +187,7 @@ __device__ void tc_stage(float* hi, float* lo, const G* p, long long sr, long lo
       for (int i = 0; i < 4; i++) {
         G v = G(0);
         if (r < nrow && k + i < kmax) v = tc_ld(p + (long long)r * sr + (long long)(k + i) * sc);
-        const float f = (float)v;
-        h[i] = tf32_hi(f);
-        l[i] = tf32_hi((float)(v - (G)h[i]));
+        tc_split((float)v, h[i], l[i]);
       }
       const int off = ((r >> 3) * TC_SBO + kq * 128 + (r & 7) * 16) >> 2;
       *reinterpret_cast<float4*>(hi + off) = make_float4(h[0], h[1], h[2], h[3]);
@@ -213,6 +221,11 @@ __device__ bool tc_gemm_tile(TcCtx& t, uint32_t col0, const GA* A, long long sar
   const size_t per = 2 * fa + 2 * fb;
   const uint32_t idesc = tc_idesc(TC_M, ncol);
   const int nchunk = (K + TC_KC - 1) / TC_KC;
+  __shared__ int skip_sh;
+  __syncthreads();
+  if (threadIdx.x == 0) skip_sh = (*(volatile int*)t.status & ST_TIMEOUT) != 0;
+  __syncthreads();
+  if (skip_sh) return false;      // an earlier wait ran out: do no more tensor-core work
   bool ok = true;
   for (int c = 0; c < nchunk; c++) {
     const int s = c & 1;
@@ -255,6 +268,175 @@ __device__ bool tc_gemm_tile(TcCtx& t, uint32_t col0, const GA* A, long long sar
   tc_fence_after();
   if (!ok && threadIdx.x == 0) atomicOr(t.status, ST_TIMEOUT);
   return ok;
+}
+
+
+// ---- operands in global memory, pre-split, in the canonical chunk order ----
+// An operand of R rows (R a multiple of 8) and K columns (a multiple of
+// TC_KC) is stored as two float arrays (hi, lo), each a sequence of K chunks
+// of R x TC_KC elements in the shared-memory layout above, so that rows
+// [r0, r0 + n) of chunk c are one contiguous run of n * TC_KC floats at
+// c * R * TC_KC + r0 * TC_KC.  Staging then is a plain bulk copy (the TMA
+// engine), with no per-element work on the SM.
+
+__device__ __forceinline__ size_t canon_index(int R, int r, int k) {
+  return (size_t)(k / TC_KC) * R * TC_KC + (size_t)(r >> 3) * (TC_SBO / 4) + ((k % TC_KC) >> 2) * 32 + (r & 7) * 4 +
+         (k & 3);
+}
+
+// Writes element (r, k) = src[r * sr + k * sc] (element type G) for r < nrow,
+// k < kvalid into the canonical (hi, lo) pair of an R x K operand; the
+// padding (rows [nrow, R), columns [kvalid, K)) is zero.  All threads.
+template <class G>
+__device__ void tc_canon(float* hi, float* lo, int R, int K, const G* src, long long sr, long long sc, int nrow,
+                         int kvalid) {
+  const long long groups = (long long)R * (K / 4);
+  if (sc == 1) {
+    for (long long e = threadIdx.x; e < groups; e += BLR_NT) {
+      const int r8 = (int)(e & 7), kq = (int)((e >> 3) % (K / 4)), rg = (int)(e / (8LL * (K / 4)));
+      const int r = rg * 8 + r8, k = kq * 4;
+      float h[4], l[4];
+#pragma unroll
+      for (int i = 0; i < 4; i++) {
+        G v = G(0);
+        if (r < nrow && k + i < kvalid) v = tc_ld(src + (long long)r * sr + (k + i));
+        tc_split((float)v, h[i], l[i]);
+      }
+      const size_t off = canon_index(R, r, k);
+      *reinterpret_cast<float4*>(hi + off) = make_float4(h[0], h[1], h[2], h[3]);
+      *reinterpret_cast<float4*>(lo + off) = make_float4(l[0], l[1], l[2], l[3]);
+    }
+  } else {
+    for (long long e = threadIdx.x; e < groups; e += BLR_NT) {
+      const int r = (int)(e % R), k = (int)(e / R) * 4;
+      float h[4], l[4];
+#pragma unroll
+      for (int i = 0; i < 4; i++) {
+        G v = G(0);
+        if (r < nrow && k + i < kvalid) v = tc_ld(src + (long long)r * sr + (long long)(k + i) * sc);
+        tc_split((float)v, h[i], l[i]);
+      }
+      const size_t off = canon_index(R, r, k);
+      *reinterpret_cast<float4*>(hi + off) = make_float4(h[0], h[1], h[2], h[3]);
+      *reinterpret_cast<float4*>(lo + off) = make_float4(l[0], l[1], l[2], l[3]);
+    }
+  }
+}
+
+// The same for a single value written by the thread that holds it (an
+// epilogue that produces an operand of the next product).
+__device__ __forceinline__ void tc_canon_put(float* hi, float* lo, int R, int r, int k, float v) {
+  const size_t off = canon_index(R, r, k);
+  float h, l;
+  tc_split(v, h, l);
+  hi[off] = h;
+  lo[off] = l;
+}
+
+// ---- bulk (TMA) copies -----------------------------------------------------
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+
+// dst (shared) <- src (global), bytes a multiple of 16, both 16-byte aligned;
+// completion is counted on the mbarrier.
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+
+// D (TC_M x n, TMEM columns [col0, col0 + n)) = sum over the nchunk K chunks
+// of A(r, k) B(c, k) for operands in the canonical global order: chunk c of A
+// is the TC_M rows at a_hi + c * a_cs (floats; same offsets in a_lo), chunk c
+// of B the n rows at b_hi + c * b_cs.  n a multiple of 16, <= 256.  Thread 0
+// runs the copy / MMA pipeline (two stages: full barriers signalled by the
+// TMA engine, empty barriers by tcgen05.commit); every thread returns after
+// the products are complete.  On a wait that runs out the status gets
+// ST_TIMEOUT and false is returned.
+struct TcBulk {
+  uint64_t* full;   // 2 mbarriers
+  uint64_t* empty;  // 2 mbarriers
+  uint32_t* ph;     // 4 parity bits: full[0], full[1], empty[0], empty[1]
+};
+
+__device__ bool tc_gemm_bulk(TcCtx& t, const TcBulk& q, uint32_t col0, const float* a_hi, const float* a_lo,
+                             size_t a_cs, const float* b_hi, const float* b_lo, size_t b_cs, int n, int nchunk) {
+  __shared__ int ok_sh;
+  if (threadIdx.x == 0) {
+    bool ok = (*(volatile int*)t.status & ST_TIMEOUT) == 0;   // after a timeout, no more work
+    asm volatile("fence.proxy.async.global;" ::: "memory");    // generic writes -> bulk-copy reads
+    const uint32_t abytes = TC_M * TC_KC * 4, bbytes = (uint32_t)n * TC_KC * 4;
+    const size_t per = 2 * (size_t)TC_M * TC_KC + 2 * (size_t)256 * TC_KC;   // floats per stage
+    const uint32_t idesc = tc_idesc(TC_M, n);
+    auto load = [&](int c, int s) {
+      float* ah = t.buf + s * per;
+      float* al = ah + TC_M * TC_KC;
+      float* bh = al + TC_M * TC_KC;
+      float* bl = bh + 256 * TC_KC;
+      mbar_expect_tx(q.full + s, 2 * abytes + 2 * bbytes);
+      bulk_g2s(ah, a_hi + c * a_cs, abytes, q.full + s);
+      bulk_g2s(al, a_lo + c * a_cs, abytes, q.full + s);
+      bulk_g2s(bh, b_hi + c * b_cs, bbytes, q.full + s);
+      bulk_g2s(bl, b_lo + c * b_cs, bbytes, q.full + s);
+    };
+    const int nc_run = ok ? nchunk : 0;
+    for (int c = 0; c < nc_run && c < 2; c++) load(c, c);
+    for (int c = 0; c < nc_run; c++) {
+      const int s = c & 1;
+      if (!mbar_wait(q.full + s, q.ph[s], t.limit_ns)) { ok = false; break; }
+      q.ph[s] ^= 1u;
+      tc_fence_after();
+      const uint32_t a0 = smem_u32(t.buf + s * per), a1 = a0 + abytes, b0 = a1 + abytes, b1 = b0 + 256 * TC_KC * 4;
+#pragma unroll
+      for (int ks = 0; ks < TC_KC / 8; ks++) {
+        const uint32_t o = ks * 256;
+        tc_mma(t.tmem + col0, tc_desc(a1 + o), tc_desc(b0 + o), idesc, (c > 0 || ks > 0) ? 1u : 0u);
+        tc_mma(t.tmem + col0, tc_desc(a0 + o), tc_desc(b1 + o), idesc, 1u);
+        tc_mma(t.tmem + col0, tc_desc(a0 + o), tc_desc(b0 + o), idesc, 1u);
+      }
+      tc_commit(q.empty + s);
+      if (c + 2 < nchunk) {
+        if (!mbar_wait(q.empty + s, q.ph[2 + s], t.limit_ns)) { ok = false; break; }
+        q.ph[2 + s] ^= 1u;
+        load(c + 2, s);
+      }
+    }
+    // the last one or two commits (their stages are not reloaded)
+    if (ok) {
+      for (int c = (nc_run >= 2 ? nc_run - 2 : 0); c < nc_run; c++) {
+        const int s = c & 1;
+        if (!mbar_wait(q.empty + s, q.ph[2 + s], t.limit_ns)) { ok = false; break; }
+        q.ph[2 + s] ^= 1u;
+      }
+    }
+    if (!ok) atomicOr(t.status, ST_TIMEOUT);
+    ok_sh = ok && nc_run == nchunk;
+  }
+  __syncthreads();
+  tc_fence_after();
+  return ok_sh != 0;
+}
+
+// Reads the TC_M x ncol accumulator 16 columns at a time and calls
+// f(row, col0, v) with v[0..15] = columns col0 .. col0 + 15 of that row
+// (each element once); lets the caller batch its global accesses.
+template <class F>
+__device__ void tc_epilogue16(const TcCtx& t, uint32_t col0, int ncol, F f) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int quarter = warp & 3, half = warp >> 2;
+  const int row = quarter * 32 + lane;
+  const int nblk = ncol / 16;
+  for (int cb = half; cb < nblk; cb += 2) {
+    float v[16];
+    tmem_ld16(t.tmem + ((uint32_t)(quarter * 32) << 16) + col0 + cb * 16, v);
+    f(row, cb * 16, v);
+  }
+  tc_fence_before();
+  __syncthreads();
 }
 
 // Reads the TC_M x ncol accumulator at TMEM columns [col0, col0 + ncol)
