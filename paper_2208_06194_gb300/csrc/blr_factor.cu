@@ -65,6 +65,10 @@ int blr_launch_factor(blr_factor* f, const blr_opts* o, cudaStream_t st) {
   }
   int rc = BLR_OK;
   SchedParams P{};
+#ifdef BLR_PHASE_TIMING
+  cudaMalloc(&P.phase, 16 * sizeof(unsigned long long));
+  cudaMemset(P.phase, 0, 16 * sizeof(unsigned long long));
+#endif
   P.prep = prep;
   P.prep_rp = prep_rp;
   P.p = p; P.q = q; P.b = b; P.cap = A.cap;
@@ -152,6 +156,16 @@ int blr_launch_factor(blr_factor* f, const blr_opts* o, cudaStream_t st) {
   cudaFree(scratch);
   cudaFree(base);
   if (prep) cudaFree(prep);
+#ifdef BLR_PHASE_TIMING
+  {
+    unsigned long long ph[16];
+    cudaMemcpy(ph, P.phase, sizeof(ph), cudaMemcpyDeviceToHost);
+    fprintf(stderr, "blr_qr phases (CTA-s):");
+    for (int i2 = 0; i2 < 16; i2++) fprintf(stderr, " %d:%.2f", i2, ph[i2] * 1e-9);
+    fprintf(stderr, "\n");
+    cudaFree(P.phase);
+  }
+#endif
   return rc;
 }
 

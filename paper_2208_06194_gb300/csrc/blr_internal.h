@@ -92,6 +92,7 @@ struct SchedParams {
   double* fvar;                  // 8 counters: their counted flops
   float* prep;                   // mixed path: per (i,k) slot, tensor-core operands of a dense Y~_ik, or NULL
   int prep_rp;                   // rows of those operands (b rounded up to 128)
+  unsigned long long* phase;     // 16 phase-time counters (builds with BLR_PHASE_TIMING only)
 };
 
 // host helpers (blr_api.cu)

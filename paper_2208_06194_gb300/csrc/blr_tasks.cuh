@@ -12,6 +12,24 @@
 #include "blr_dag.h"
 #include "blr_tc.cuh"
 
+// Optional per-phase timing of the task bodies (a build with
+// -DBLR_PHASE_TIMING; summed CTA time per phase, printed by blr_qr).
+#ifdef BLR_PHASE_TIMING
+#define PH(id, ...)                                                              \
+  do {                                                                           \
+    __syncthreads();                                                             \
+    const unsigned long long ph_t0_ = tc_gtimer();                               \
+    __VA_ARGS__;                                                                 \
+    __syncthreads();                                                             \
+    if (threadIdx.x == 0) atomicAdd(env.P->phase + (id), tc_gtimer() - ph_t0_); \
+  } while (0)
+#else
+#define PH(id, ...) \
+  do {              \
+    __VA_ARGS__;    \
+  } while (0)
+#endif
+
 namespace {
 
 // Bump allocator over the CTA's private scratch slab.  The slab holds
@@ -141,7 +159,7 @@ __device__ void recompress_side(TaskEnv& env, S* Uf, int ldu, const S* H, const 
   copy_mat(U0, b, Uf, ldu, b, s);
   S* TU = (S*)env.alloc(((size_t)BLR_NB * s * sizeof(S) + 7) / 8);
   __syncthreads();
-  geqrf(Uf, ldu, b, s, TU, c);
+  PH(9, geqrf(Uf, ldu, b, s, TU, c));
   S* RU = (S*)env.alloc(((size_t)s * s * sizeof(S) + 7) / 8);
   S* RH = (S*)env.alloc(((size_t)s * s * sizeof(S) + 7) / 8);
   for (int e = threadIdx.x; e < s * s; e += BLR_NT) {
@@ -158,7 +176,8 @@ __device__ void recompress_side(TaskEnv& env, S* Uf, int ldu, const S* H, const 
   const double tol2 = P.rec_tol * P.rec_tol * nrm2;
   S* tauM = (S*)env.alloc(((size_t)s * sizeof(S) + 7) / 8);
   int* perm = c.s.ivec;
-  const int r = qrcp(M, s, s, s, tol2, P.dense_rank, perm, tauM, c.s.flag + 2, c);
+  int r = 0;
+  PH(10, r = qrcp(M, s, s, s, tol2, P.dense_rank, perm, tauM, c.s.flag + 2, c));
   const int over = c.s.flag[2];
   __syncthreads();
   if (over) {
@@ -181,9 +200,8 @@ __device__ void recompress_side(TaskEnv& env, S* Uf, int ldu, const S* H, const 
       CV[perm[cc] + (size_t)l * b] = (cc >= l) ? M[l + (size_t)cc * s] : S(0);
     }
     __syncthreads();
-    apply_q_unblocked(M, s, s, r, tauM, CU, b, r, false, c);
-    apply_q<S>(Uf, ldu, b, s, TU, CU, b, r, false, c);
-    apply_q<S>(H, b, b, s, TH, CV, b, r, false, c);
+    PH(11, apply_q_unblocked(M, s, s, r, tauM, CU, b, r, false, c); apply_q<S>(Uf, ldu, b, s, TU, CU, b, r, false, c);
+           apply_q<S>(H, b, b, s, TH, CV, b, r, false, c));
     copy_mat(dest, b, CU, b, b, r);
     copy_mat(dest + (size_t)b * P.cap, b, CV, b, b, r);
   }
@@ -482,7 +500,7 @@ __device__ void task_tsqrt(TaskEnv& env, int i, int k, Ctx& c) {
         release_task(P, *env.dag, sid);
         env.skip_succ = sid;
       }
-      tsqrt_prep(env, i, k, c);
+      PH(7, tsqrt_prep(env, i, k, c));
     }
   }
 }
@@ -525,11 +543,11 @@ __device__ void tpmqrt_core(TaskEnv& env, S* Yt, int rY, const S* Tik, S* Rt, in
     copy_mat(G, ldG, Rt, b, b, rR);                              // U_R
     copy_mat(H, b, Rt + (size_t)b * cap, b, b, rR);              // V_R
     if (!adense) {
-      if (ylr) gemm(ry, rA, b, S(1), Uy, b, true, At, b, false, S(0), G + b + (size_t)rR * ldG, ldG, c);
+      if (ylr) PH(2, gemm(ry, rA, b, S(1), Uy, b, true, At, b, false, S(0), G + b + (size_t)rR * ldG, ldG, c));
       else copy_mat(G + b + (size_t)rR * ldG, ldG, At, b, b, rA);
       copy_mat(H + (size_t)rR * b, b, At + (size_t)b * cap, b, b, rA);
     } else {
-      gemm(b, ry, b, S(1), At, b, true, Uy, b, false, S(0), H + (size_t)rR * b, b, c);
+      PH(2, gemm(b, ry, b, S(1), At, b, true, Uy, b, false, S(0), H + (size_t)rR * b, b, c));
       __syncthreads();
       for (int e = threadIdx.x; e < ry; e += BLR_NT) G[b + e + (size_t)(rR + e) * ldG] = S(1);
     }
@@ -537,7 +555,7 @@ __device__ void tpmqrt_core(TaskEnv& env, S* Yt, int rY, const S* Tik, S* Rt, in
     copy_mat(PU0, ry, G + b + (size_t)rR * ldG, ldG, ry, s2);
     copy_mat(H0, b, H, b, b, s);
     __syncthreads();
-    apply_ts_reflector<S>(Yr, ry, b, Tik, G, ldG, colmajor(G + b, ldG), s, true, c);
+    PH(3, apply_ts_reflector<S>(Yr, ry, b, Tik, G, ldG, colmajor(G + b, ldG), s, true, c));
     for (int e = threadIdx.x; e < ry * s2; e += BLR_NT) {
       int a = e % ry, l = e / ry;
       G[b + a + (size_t)(rR + l) * ldG] -= PU0[e];
@@ -546,7 +564,7 @@ __device__ void tpmqrt_core(TaskEnv& env, S* Yt, int rY, const S* Tik, S* Rt, in
     S* TH = alloc((size_t)BLR_NB * s);
     if (!adense) {
       S* UfA = alloc((size_t)b * s);
-      if (ylr) gemm(b, s, ry, S(1), Uy, b, false, G + b, ldG, false, S(0), UfA, b, c);
+      if (ylr) PH(2, gemm(b, s, ry, S(1), Uy, b, false, G + b, ldG, false, S(0), UfA, b, c));
       else copy_mat(UfA, b, G + b, ldG, b, s);
       __syncthreads();
       for (int e = threadIdx.x; e < b * rA; e += BLR_NT) {
@@ -554,15 +572,15 @@ __device__ void tpmqrt_core(TaskEnv& env, S* Yt, int rY, const S* Tik, S* Rt, in
         UfA[a + (size_t)(rR + l) * b] += ldg(At + a + (size_t)l * b);
       }
       __syncthreads();
-      geqrf(H, b, b, s, TH, c);
-      recompress_side(env, G, ldG, H, TH, H0, s, Rt, nR, c);
-      recompress_side(env, UfA, b, H, TH, H0, s, At, nA, c);
+      PH(4, geqrf(H, b, b, s, TH, c));
+      PH(5, recompress_side(env, G, ldG, H, TH, H0, s, Rt, nR, c));
+      PH(5, recompress_side(env, UfA, b, H, TH, H0, s, At, nA, c));
     } else {
       S* M1 = alloc((size_t)b * s);
-      gemm(b, s, ry, S(1), Uy, b, false, G + b, ldG, false, S(0), M1, b, c);
-      gemm(b, b, s, S(1), M1, b, false, H0, b, true, S(1), At, b, c);
-      geqrf(H, b, b, s, TH, c);
-      recompress_side(env, G, ldG, H, TH, H0, s, Rt, nR, c);
+      PH(2, gemm(b, s, ry, S(1), Uy, b, false, G + b, ldG, false, S(0), M1, b, c));
+      PH(2, gemm(b, b, s, S(1), M1, b, false, H0, b, true, S(1), At, b, c));
+      PH(4, geqrf(H, b, b, s, TH, c));
+      PH(5, recompress_side(env, G, ldG, H, TH, H0, s, Rt, nR, c));
     }
     return;
   }
@@ -574,7 +592,7 @@ __device__ void tpmqrt_core(TaskEnv& env, S* Yt, int rY, const S* Tik, S* Rt, in
     Rd = Rt;
   } else {
     Rd = alloc((size_t)b * b);
-    if (rR > 0) gemm(b, b, rR, S(1), Rt, b, false, Rt + (size_t)b * cap, b, true, S(0), Rd, b, c);
+    if (rR > 0) PH(2, gemm(b, b, rR, S(1), Rt, b, false, Rt + (size_t)b * cap, b, true, S(0), Rd, b, c));
     else zero_mat(Rd, b, b, b);
     r_scratch = true;
   }
@@ -586,13 +604,13 @@ __device__ void tpmqrt_core(TaskEnv& env, S* Yt, int rY, const S* Tik, S* Rt, in
     ldp = ry;
     Pm = alloc((size_t)ry * b);
     if (rA < 0) {
-      gemm(ry, b, b, S(1), Uy, b, true, At, b, false, S(0), Pm, ry, c);
+      PH(2, gemm(ry, b, b, S(1), Uy, b, true, At, b, false, S(0), Pm, ry, c));
     } else if (rA == 0) {
       zero_mat(Pm, ry, ry, b);
     } else {
       S* PU = alloc((size_t)ry * rA);
-      gemm(ry, rA, b, S(1), Uy, b, true, At, b, false, S(0), PU, ry, c);
-      gemm(ry, b, rA, S(1), PU, ry, false, At + (size_t)b * cap, b, true, S(0), Pm, ry, c);
+      PH(2, gemm(ry, rA, b, S(1), Uy, b, true, At, b, false, S(0), PU, ry, c));
+      PH(2, gemm(ry, b, rA, S(1), PU, ry, false, At + (size_t)b * cap, b, true, S(0), Pm, ry, c));
     }
     P0 = alloc((size_t)ry * b);
     __syncthreads();
@@ -604,12 +622,12 @@ __device__ void tpmqrt_core(TaskEnv& env, S* Yt, int rY, const S* Tik, S* Rt, in
       a_inplace = true;
     } else {
       Pm = alloc((size_t)b * b);
-      if (rA > 0) gemm(b, b, rA, S(1), At, b, false, At + (size_t)b * cap, b, true, S(0), Pm, b, c);
+      if (rA > 0) PH(2, gemm(b, b, rA, S(1), At, b, false, At + (size_t)b * cap, b, true, S(0), Pm, b, c));
       else zero_mat(Pm, b, b, b);
     }
   }
   __syncthreads();
-  apply_ts_reflector<S>(Yr, ry, b, Tik, Rd, b, colmajor(Pm, ldp), b, true, c);
+  PH(3, apply_ts_reflector<S>(Yr, ry, b, Tik, Rd, b, colmajor(Pm, ldp), b, true, c));
   if (r_scratch) {
     copy_mat(Rt, b, Rd, b, b, b);
     __syncthreads();
@@ -628,7 +646,7 @@ __device__ void tpmqrt_core(TaskEnv& env, S* Yt, int rY, const S* Tik, S* Rt, in
   for (int e = threadIdx.x; e < ry * b; e += BLR_NT) Pm[e] -= P0[e];
   __syncthreads();
   if (rA < 0) {
-    gemm(b, b, ry, S(1), Uy, b, false, Pm, ry, false, S(1), At, b, c);
+    PH(2, gemm(b, b, ry, S(1), Uy, b, false, Pm, ry, false, S(1), At, b, c));
     return;
   }
   const int s = rA + ry;
@@ -647,8 +665,8 @@ __device__ void tpmqrt_core(TaskEnv& env, S* Yt, int rY, const S* Tik, S* Rt, in
   copy_mat(H0, b, H, b, b, s);
   S* TH = alloc((size_t)BLR_NB * s);
   __syncthreads();
-  geqrf(H, b, b, s, TH, c);
-  recompress_side(env, Uf, b, H, TH, H0, s, At, nA, c);
+  PH(4, geqrf(H, b, b, s, TH, c));
+  PH(5, recompress_side(env, Uf, b, H, TH, H0, s, At, nA, c));
 }
 
 
@@ -851,8 +869,8 @@ __device__ void task_tpmqrt(TaskEnv& env, int i, int j, int k, Ctx& c) {
   }
   if (rY == 0) return;
   if (rY < 0 && (rR < 0 || rA < 0) && env.tc) {
-    tpmqrt_tc_dense(env, Yt, Tik, P.prep ? prep_ptr(P, i, k) : nullptr, Rt, rR, At, rA, rank_ptr(P, k, j),
-                    rank_ptr(P, i, j), c);
+    PH(6, tpmqrt_tc_dense(env, Yt, Tik, P.prep ? prep_ptr(P, i, k) : nullptr, Rt, rR, At, rA,
+                          rank_ptr(P, k, j), rank_ptr(P, i, j), c));
     return;
   }
   // mixed: FP32 copies of the operands, FP32 arithmetic, results back to FP64
@@ -860,18 +878,15 @@ __device__ void task_tpmqrt(TaskEnv& env, int i, int j, int k, Ctx& c) {
   float* Tf = (float*)env.alloc((size_t)BLR_NB * b / 2);
   float* Rf = (float*)env.alloc((size_t)b * b / 2);
   float* Af = (float*)env.alloc((size_t)b * b / 2);
-  copy_tile(Yf, Yt, rY, b, cap);
-  copy_mat(Tf, BLR_NB, Tik, BLR_NB, BLR_NB, b);
-  copy_tile(Rf, Rt, rR, b, cap);
-  copy_tile(Af, At, rA, b, cap);
+  PH(0, copy_tile(Yf, Yt, rY, b, cap); copy_mat(Tf, BLR_NB, Tik, BLR_NB, BLR_NB, b);
+        copy_tile(Rf, Rt, rR, b, cap); copy_tile(Af, At, rA, b, cap));
   __shared__ int newr[2];
   if (threadIdx.x == 0) { newr[0] = rR; newr[1] = rA; }
   __syncthreads();
   tpmqrt_core<float>(env, Yf, rY, Tf, Rf, rR, Af, rA, &newr[0], &newr[1], c);
   __syncthreads();
   const int r1 = newr[0], r2 = newr[1];
-  copy_tile(Rt, Rf, r1, b, cap);
-  copy_tile(At, Af, r2, b, cap);
+  PH(1, copy_tile(Rt, Rf, r1, b, cap); copy_tile(At, Af, r2, b, cap));
   __syncthreads();
   if (threadIdx.x == 0) {
     *rank_ptr(P, k, j) = r1;
