@@ -123,20 +123,33 @@ __device__ __forceinline__ View<T> colmajor(T* p, long long ld) { return View<T>
 template <class T>
 __device__ __forceinline__ View<T> rowmajor(T* p, long long ld) { return View<T>{p, ld, 1}; }
 
+// Element loops over [0, tot) in CTA-size steps, kMLP elements per thread
+// at a time with every load issued before the first use: with one CTA of
+// eight warps per SM, a loop that waits on one load at a time is bound by
+// memory latency, not bandwidth.
+constexpr int kMLP = 4;
+
 // dst (shared, column-major ldd, type S) = src (rows x cols); coalesced along src's unit stride.
 template <class S, class G>
 __device__ void stage_in(S* dst, int ldd, View<G> src, int rows, int cols) {
   const int tot = rows * cols;
-  if (src.sr == 1) {
-    for (int e = threadIdx.x; e < tot; e += BLR_NT) {
-      int r = e % rows, c = e / rows;
-      dst[r + c * ldd] = (S)ldg(src.at(r, c));
+  const bool colwise = src.sr == 1;
+  for (int base = 0; base < tot; base += BLR_NT * kMLP) {
+    G v[kMLP];
+    int off[kMLP];
+#pragma unroll
+    for (int u = 0; u < kMLP; u++) {
+      const int e = base + u * BLR_NT + threadIdx.x;
+      int r = 0, c = 0;
+      if (e < tot) {
+        if (colwise) { r = e % rows; c = e / rows; } else { c = e % cols; r = e / cols; }
+      }
+      off[u] = r + c * ldd;
+      v[u] = (e < tot) ? ldg(src.at(r, c)) : G(0);
     }
-  } else {
-    for (int e = threadIdx.x; e < tot; e += BLR_NT) {
-      int c = e % cols, r = e / cols;
-      dst[r + c * ldd] = (S)ldg(src.at(r, c));
-    }
+#pragma unroll
+    for (int u = 0; u < kMLP; u++)
+      if (base + u * BLR_NT + (int)threadIdx.x < tot) dst[off[u]] = (S)v[u];
   }
 }
 
@@ -159,18 +172,29 @@ __device__ void stage_out(View<G> dst, const S* src, int lds, int rows, int cols
 // Global-to-global copy (with conversion) / zero of a rows x cols block.
 template <class D, class Src>
 __device__ void copy_mat(D* dst, long long ldd, const Src* src, long long lds, int rows, int cols) {
-  const long long tot = (long long)rows * cols;
-  for (long long e = threadIdx.x; e < tot; e += BLR_NT) {
-    int r = (int)(e % rows), c = (int)(e / rows);
-    dst[r + c * ldd] = (D)ldg(src + r + c * lds);
+  const int tot = rows * cols;
+  for (int base = 0; base < tot; base += BLR_NT * kMLP) {
+    Src v[kMLP];
+    long long od[kMLP];
+#pragma unroll
+    for (int u = 0; u < kMLP; u++) {
+      const int e = base + u * BLR_NT + threadIdx.x;
+      int r = 0, c = 0;
+      if (e < tot) { r = e % rows; c = e / rows; }
+      od[u] = r + c * ldd;
+      v[u] = (e < tot) ? ldg(src + r + c * lds) : Src(0);
+    }
+#pragma unroll
+    for (int u = 0; u < kMLP; u++)
+      if (base + u * BLR_NT + (int)threadIdx.x < tot) dst[od[u]] = (D)v[u];
   }
 }
 
 template <class D>
 __device__ void zero_mat(D* dst, long long ldd, int rows, int cols) {
-  const long long tot = (long long)rows * cols;
-  for (long long e = threadIdx.x; e < tot; e += BLR_NT) {
-    int r = (int)(e % rows), c = (int)(e / rows);
+  const int tot = rows * cols;
+  for (int e = threadIdx.x; e < tot; e += BLR_NT) {
+    const int r = e % rows, c = e / rows;
     dst[r + c * ldd] = D(0);
   }
 }
@@ -316,10 +340,7 @@ __device__ void apply_refl_panel(G* C, long long ldc, int h, int nc, const S* P,
     for (int r0 = 0; r0 < h; r0 += BLR_RB) {
       const int rb = min(BLR_RB, h - r0);
       __syncthreads();
-      for (int e = threadIdx.x; e < rb * cw; e += BLR_NT) {
-        int rr = e % rb, ll = e / rb;
-        Cs[rr + ll * ldcs] = (S)ldg(C + (r0 + rr) + (long long)(c0 + ll) * ldc);
-      }
+      stage_in(Cs, ldcs, colmajor(C + r0 + (long long)c0 * ldc, ldc), rb, cw);
       __syncthreads();
       if (a < w) {
         for (int rr = 0; rr < rb; rr++) {
@@ -393,17 +414,7 @@ __device__ void apply_refl_ts(GT* Ct, long long ldt, View<GB> Cb, int ry, int nc
     for (int r0 = 0; r0 < ry; r0 += BLR_RB) {
       const int rb = min(BLR_RB, ry - r0);
       __syncthreads();
-      if (Cb.sr == 1) {
-        for (int e = threadIdx.x; e < rb * cw; e += BLR_NT) {
-          int rr = e % rb, ll = e / rb;
-          Cs[rr + ll * ldcs] = (S)ldg(Cb.at(r0 + rr, c0 + ll));
-        }
-      } else {
-        for (int e = threadIdx.x; e < rb * cw; e += BLR_NT) {
-          int ll = e % cw, rr = e / cw;
-          Cs[rr + ll * ldcs] = (S)ldg(Cb.at(r0 + rr, c0 + ll));
-        }
-      }
+      stage_in(Cs, ldcs, Cb.shifted(r0, c0), rb, cw);
       __syncthreads();
       if (a < w) {
         for (int rr = 0; rr < rb; rr++) {

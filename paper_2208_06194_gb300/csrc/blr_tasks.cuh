@@ -177,7 +177,19 @@ __device__ void recompress_side(TaskEnv& env, S* Uf, int ldu, const S* H, const 
   S* tauM = (S*)env.alloc(((size_t)s * sizeof(S) + 7) / 8);
   int* perm = c.s.ivec;
   int r = 0;
-  PH(10, r = qrcp(M, s, s, s, tol2, P.dense_rank, perm, tauM, c.s.flag + 2, c));
+  if ((size_t)s * s * sizeof(S) <= (size_t)BLR_SM_PNL * sizeof(double)) {
+    // the core fits in shared memory (the panel buffer is idle here): the
+    // pivoted QR's many dependent passes then run at shared-memory latency
+    S* Ms = as<S>(c.s.pnl);
+    __syncthreads();
+    copy_mat(Ms, s, M, s, s, s);
+    __syncthreads();
+    PH(10, r = qrcp(Ms, s, s, s, tol2, P.dense_rank, perm, tauM, c.s.flag + 2, c));
+    stage_out(colmajor(M, s), Ms, s, s, s);
+    __syncthreads();
+  } else {
+    PH(10, r = qrcp(M, s, s, s, tol2, P.dense_rank, perm, tauM, c.s.flag + 2, c));
+  }
   const int over = c.s.flag[2];
   __syncthreads();
   if (over) {
