@@ -2,10 +2,13 @@
 65536 x 32768 Yukawa kernel matrix (b = 512), with the fraction of the
 roofline reached by the factorization kernel, the residual and
 orthogonality of the result, an end-to-end number through host buffers,
-and the CPU oracle timed on a bounded sample.
+and the CPU oracle timed on a bounded sample.  The headline is the
+mixed-precision factorization; at N = 1 the FP64 factorization of the same
+matrix at the same tolerance is timed beside it (both meet
+||A - QR||/||A|| <= 10 tol, the stated residual).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                    [--precision fp64|mixed] [--tol 1e-6] [--size full|small]
+                    [--precision mixed|fp64] [--tol 1e-5] [--size full|small]
 
 N > 1 runs N independent replicas (one per GPU, launched by torchrun); the
 single-matrix factorization does not shard.  Prints one JSON line on rank 0.
@@ -33,6 +36,46 @@ PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 # (the nominal 1.25 TFLOP/s FP64 of GB300); FP32 SIMT: 152 x 128 x 2 x 2.07 GHz.
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+# TF32 tensor peak: the measured dense bf16 rate x the nominal TF32/BF16 ratio
+# (1.1 / 2.25 PFLOP/s); a 3xTF32 product issues three MMAs, so the rate of
+# algorithmic flops is a third of it.
+TF32_OVER_BF16 = 1.1 / 2.25
+
+
+def measured_bf16_tflops():
+    try:
+        with open(PEAKS_FILE) as fh:
+            return float(json.load(fh)["bf16_tflops"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 1900.0, "fallback"
+
+
+def roofline(st, k_sec, prec_is_fp64):
+    """Roofline of the factorization kernel for its own mix of work.
+    FP64: every counted flop on the FP64 ALUs.  Mixed: the updates that run
+    on the tensor cores (a dense reflector block with a dense R_kj or A_ij)
+    at the 3xTF32 rate, every other counted flop at the FP32 SIMT rate; the
+    bound is the sum of the two times and the peak is total flops / bound."""
+    flops = st["flops"][4]
+    achieved = flops / k_sec / 1e12
+    if prec_is_fp64:
+        peak = FP64_PEAK_TFLOPS
+        return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": None, "peak_note": "FP64 ALU nominal 1.26 TFLOP/s (152 SMs x 2 DFMA/clk x 2.07 GHz)",
+                "kernel": "k_factor (persistent scheduler)", "flops_counted": flops}
+    bf16, src = measured_bf16_tflops()
+    p_tc = bf16 * TF32_OVER_BF16 / 3.0
+    f_tc = sum(st["tpmqrt_kind_flops"][v] for v in (5, 6, 7))     # Y~ dense and R_kj or A_ij dense
+    t_bound = f_tc / (p_tc * 1e12) + (flops - f_tc) / (FP32_PEAK_TFLOPS * 1e12)
+    peak = flops / t_bound / 1e12
+    return {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": t_bound / k_sec,
+            "traffic": None,
+            "peak_note": (f"mix of this run: {f_tc / 1e12:.1f} TFLOP at the 3xTF32 rate ({p_tc:.0f} TFLOP/s = "
+                          f"{src} bf16 {bf16:.0f} x 1.1/2.25 / 3) + {(flops - f_tc) / 1e12:.1f} TFLOP at the FP32 "
+                          f"SIMT rate ({FP32_PEAK_TFLOPS:.1f} TFLOP/s); peak = flops / summed bound time"),
+            "kernel": "k_factor (persistent scheduler)", "flops_counted": flops,
+            "tensor_part": {"tflop": f_tc / 1e12,
+                            "cta_seconds": sum(st["tpmqrt_kind_seconds"][v] for v in (5, 6, 7))}}
 
 SIZES = {
     "full": dict(m=65536, n=32768, b=512, seed_x=301, seed_y=302),
@@ -46,14 +89,15 @@ def parse():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
-    ap.add_argument("--tol", type=float, default=1e-6)
+    ap.add_argument("--precision", default="mixed", choices=["fp64", "mixed"])
+    ap.add_argument("--tol", type=float, default=1e-5)
     ap.add_argument("--dense-rank", type=int, default=128)
     ap.add_argument("--size", default="full", choices=list(SIZES))
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--compare-fp64", action="store_true",
-                    help="also time one FP64 factorization for the mixed-vs-FP64 comparison")
+    ap.add_argument("--no-compare-fp64", action="store_true",
+                    help="skip the FP64 factorization timed beside the mixed one (N = 1)")
+    ap.add_argument("--scratch-b2", type=int, default=0, help="per-CTA scratch in units of b*b doubles")
     return ap.parse_args()
 
 
@@ -261,7 +305,8 @@ def main():
     s = SIZES[args.size]
     pr = W.yukawa3d(s["m"], s["n"], s["b"], s["seed_x"] + 1000 * rank, s["seed_y"] + 1000 * rank)
     prec = blr.BLR_PREC_MIXED if args.precision == "mixed" else blr.BLR_PREC_FP64
-    opts = blr.blr_opts_default(b=s["b"], tol=args.tol, precision=prec, dense_rank=args.dense_rank)
+    opts = blr.blr_opts_default(b=s["b"], tol=args.tol, precision=prec, dense_rank=args.dense_rank,
+                                scratch_b2=args.scratch_b2)
     a0 = blr.blr_compress_kernel(pr.x, pr.y, "yukawa3d", opts)
     st_a = blr.blr_stats(a0)
     stream = torch.cuda.current_stream()
@@ -308,14 +353,15 @@ def main():
 
     # FP64 comparison at the same tolerance (mixed runs only)
     fp64 = None
-    if args.compare_fp64 and prec == blr.BLR_PREC_MIXED:
+    if not args.no_compare_fp64 and prec == blr.BLR_PREC_MIXED and world == 1:
         o64 = blr.blr_opts_default(b=s["b"], tol=args.tol, precision=blr.BLR_PREC_FP64,
-                                   dense_rank=args.dense_rank)
+                                   dense_rank=args.dense_rank, scratch_b2=args.scratch_b2)
         f64, t64 = one_step(o64)
         r64 = probes(blr, f64, a0, pr, torch, dev)
         st64 = blr.blr_stats(f64)
         fp64 = {"seconds": t64, "res_A": r64[0], "res_At": r64[1], "orth": r64[2],
-                "gflops_counted": st64["flops"][4] / 1e9}
+                "gflops_counted": st64["flops"][4] / 1e9,
+                "meets_10tol": bool(r64[0] <= 10 * args.tol), "mixed_speedup": t64 / t_step}
         f64.destroy()
 
     # end to end through host buffers: import (H2D) + blr_qr + export (D2H)
@@ -353,14 +399,12 @@ def main():
         if world > 1:
             dist.destroy_process_group()
         return
-    flops = st["flops"][4]
     k_sec = statistics.median(kern)
-    achieved = flops / k_sec / 1e12
-    peak = FP64_PEAK_TFLOPS if prec == blr.BLR_PREC_FP64 else FP32_PEAK_TFLOPS
     line = {
         "metric": METRIC, "value": t_step / world, "unit": "s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_step * 1e3, "higher_is_better": False,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64" if prec == 0 else "f64+f32",
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64" if prec == 0 else "f64 panels + 3xtf32/f32 updates",
         "data": "synthetic",
         "config": {"workload": workload_name(args), "global_batch": world, "precision": args.precision,
                    "dense_rank": args.dense_rank, "parallelism": "replicas" if world > 1 else "single",
@@ -371,11 +415,7 @@ def main():
         "kernel_seconds": k_sec,
         "task_cta_seconds": dict(zip(["geqrt", "larfb", "tsqrt", "tpmqrt"], st["task_seconds"])),
         "tpmqrt_kinds": tpmqrt_kinds(st),
-        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                     "frac": achieved / peak, "traffic": None,
-                     "peak_note": ("FP64 ALU nominal 1.26 TFLOP/s (152 SMs x 2 DFMA/clk x 2.07 GHz)"
-                                   if prec == 0 else "FP32 SIMT nominal (152 x 128 FMA/clk x 2.07 GHz)"),
-                     "kernel": "k_factor (persistent scheduler)", "flops_counted": flops},
+        "roofline": roofline(st, k_sec, prec == blr.BLR_PREC_FP64),
         "clocks": clk,
         "gpu_launches": args.steps,
         "e2e": e2e,

@@ -64,6 +64,10 @@ typedef struct blr_factor blr_factor; /* opaque factor: in-place R/Y~ tiles + T 
  *  sched_ctas   persistent scheduler CTAs; 0 = one per SM.
  *  watchdog_ms  the scheduler gives up (BLR_ERR_TIMEOUT) after this many
  *               milliseconds without any task completing; 0 = 20000.
+ *  scratch_b2   private scratch per scheduler CTA, in units of b*b doubles;
+ *               0 = 20 (ample for every rank up to b/2).  A task that needs
+ *               more fails the call with BLR_ERR_RANK_OVERFLOW (blr_stats
+ *               reports the largest use, scratch_peak_bytes).
  */
 typedef struct blr_opts {
   int b;
@@ -74,7 +78,8 @@ typedef struct blr_opts {
   int precision;
   int sched_ctas;
   int watchdog_ms;
-  int reserved[8];
+  int scratch_b2;
+  int reserved[7];
 } blr_opts;
 
 /* Statistics of a handle (host struct filled by blr_stats). */
@@ -93,6 +98,8 @@ typedef struct blr_stats_t {
                                4 (Y~_ik dense) + 2 (R_kj dense) + (A_ij dense) at task start */
   double tpmqrt_kind_seconds[8]; /* factor only: their summed durations (CTA-seconds) */
   double tpmqrt_kind_flops[8];   /* factor only: their counted FP ops */
+  long long scratch_peak_bytes;  /* factor only: largest per-CTA scratch use of any task */
+  long long scratch_bytes;       /* factor only: per-CTA scratch slabs allocated (all CTAs) */
 } blr_stats_t;
 
 /* Fills *opts with the defaults (b = 512, tol = 1e-8, FP64). */

@@ -33,7 +33,7 @@ class Opts(ctypes.Structure):
     _fields_ = [("b", ctypes.c_int), ("fixed_rank", ctypes.c_int), ("tol", ctypes.c_double),
                 ("rec_tol", ctypes.c_double), ("dense_rank", ctypes.c_int),
                 ("precision", ctypes.c_int), ("sched_ctas", ctypes.c_int),
-                ("watchdog_ms", ctypes.c_int), ("reserved", ctypes.c_int * 8)]
+                ("watchdog_ms", ctypes.c_int), ("scratch_b2", ctypes.c_int), ("reserved", ctypes.c_int * 7)]
 
 
 class Stats(ctypes.Structure):
@@ -43,7 +43,8 @@ class Stats(ctypes.Structure):
                 ("flops", ctypes.c_double * 5), ("tasks", ctypes.c_longlong * 4),
                 ("task_seconds", ctypes.c_double * 4), ("seconds", ctypes.c_double),
                 ("tpmqrt_kind", ctypes.c_longlong * 8), ("tpmqrt_kind_seconds", ctypes.c_double * 8),
-                ("tpmqrt_kind_flops", ctypes.c_double * 8)]
+                ("tpmqrt_kind_flops", ctypes.c_double * 8), ("scratch_peak_bytes", ctypes.c_longlong),
+                ("scratch_bytes", ctypes.c_longlong)]
 
 
 _lib = None

@@ -92,7 +92,7 @@ static void free_matrix_storage(blr_matrix* a) {
 
 static int check_opts(const blr_opts* o) {
   if (!o) { blr_set_error("opts is NULL"); return BLR_ERR_INVALID; }
-  if (o->fixed_rank < 0 || o->tol < 0 || o->rec_tol < 0 || o->dense_rank < 0) {
+  if (o->fixed_rank < 0 || o->tol < 0 || o->rec_tol < 0 || o->dense_rank < 0 || o->scratch_b2 < 0) {
     blr_set_error("negative option value");
     return BLR_ERR_INVALID;
   }
@@ -283,6 +283,8 @@ extern "C" int blr_stats(const void* handle, int handle_is_factor, blr_stats_t* 
     for (int t = 0; t < 4; t++) out->tasks[t] = f->tasks[t];
     for (int t = 0; t < 4; t++) out->task_seconds[t] = f->task_seconds[t];
     out->seconds = f->seconds;
+    out->scratch_peak_bytes = f->scratch_peak_bytes;
+    out->scratch_bytes = f->scratch_bytes;
     for (int v = 0; v < 8; v++) {
       out->tpmqrt_kind[v] = f->tpmqrt_kind[v];
       out->tpmqrt_kind_seconds[v] = f->tpmqrt_kind_seconds[v];

@@ -29,7 +29,7 @@ int blr_launch_factor(blr_factor* f, const blr_opts* o, cudaStream_t st) {
 
   const int nsm = blr_num_sms();
   int ctas = o->sched_ctas > 0 ? o->sched_ctas : nsm;
-  const size_t slab = (size_t)BLR_SLAB_B2 * b * b;
+  const size_t slab = (size_t)(o->scratch_b2 > 0 ? o->scratch_b2 : BLR_SLAB_B2) * b * b;
 
   // one device block for all scheduler state
   size_t bytes = 0;
@@ -42,7 +42,7 @@ int blr_launch_factor(blr_factor* f, const blr_opts* o, cudaStream_t st) {
                o_prog = take(sizeof(unsigned long long)), o_flops = take(sizeof(double) * 4),
                o_ntask = take(sizeof(unsigned long long) * 4), o_tns = take(sizeof(unsigned long long) * 4),
                o_nvar = take(sizeof(unsigned long long) * 8), o_tvar = take(sizeof(unsigned long long) * 8),
-               o_fvar = take(sizeof(double) * 8);
+               o_fvar = take(sizeof(double) * 8), o_peak = take(sizeof(unsigned long long));
   char* base = nullptr;
   double* scratch = nullptr;
   if (cudaMalloc(&base, bytes) != cudaSuccess) { blr_set_error("blr_qr: out of device memory (scheduler state)"); return BLR_ERR_OOM; }
@@ -97,6 +97,7 @@ int blr_launch_factor(blr_factor* f, const blr_opts* o, cudaStream_t st) {
   P.nvar = (unsigned long long*)(base + o_nvar);
   P.tvar = (unsigned long long*)(base + o_tvar);
   P.fvar = (double*)(base + o_fvar);
+  P.slab_peak = (unsigned long long*)(base + o_peak);
 
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   do {
@@ -134,6 +135,10 @@ int blr_launch_factor(blr_factor* f, const blr_opts* o, cudaStream_t st) {
     cudaMemcpy(nv, P.nvar, sizeof(nv), cudaMemcpyDeviceToHost);
     cudaMemcpy(tv, P.tvar, sizeof(tv), cudaMemcpyDeviceToHost);
     cudaMemcpy(fv, P.fvar, sizeof(fv), cudaMemcpyDeviceToHost);
+    unsigned long long peak = 0;
+    cudaMemcpy(&peak, P.slab_peak, sizeof(peak), cudaMemcpyDeviceToHost);
+    f->scratch_peak_bytes = (long long)(peak * sizeof(double));
+    f->scratch_bytes = (long long)(sizeof(double) * slab * ctas);
     for (int v = 0; v < 8; v++) {
       f->tpmqrt_kind[v] = (long long)nv[v];
       f->tpmqrt_kind_seconds[v] = tv[v] * 1e-9;

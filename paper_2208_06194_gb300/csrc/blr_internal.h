@@ -59,6 +59,8 @@ struct blr_factor {
   long long tpmqrt_kind[8];
   double tpmqrt_kind_seconds[8];
   double tpmqrt_kind_flops[8];
+  long long scratch_peak_bytes;
+  long long scratch_bytes;
   double seconds;
 };
 
@@ -93,6 +95,7 @@ struct SchedParams {
   float* prep;                   // mixed path: per (i,k) slot, tensor-core operands of a dense Y~_ik, or NULL
   int prep_rp;                   // rows of those operands (b rounded up to 128)
   unsigned long long* phase;     // 16 phase-time counters (builds with BLR_PHASE_TIMING only)
+  unsigned long long* slab_peak; // largest scratch use of any task (doubles)
 };
 
 // host helpers (blr_api.cu)

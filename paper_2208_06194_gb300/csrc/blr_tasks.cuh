@@ -45,6 +45,7 @@ struct TaskEnv {
   const TcBulk* tq;   // its bulk-copy pipeline barriers
   const DagShape* dag;
   int skip_succ;      // a successor the task body has already released (-1: none)
+  size_t peak;        // high-water mark of used (doubles)
   __device__ double* alloc(size_t n) {
     const size_t nn = (n + 31) & ~(size_t)31;   // 256-byte granules
     if (used + nn > P->slab) {
@@ -53,6 +54,7 @@ struct TaskEnv {
     }
     double* p = slab + used;
     used += nn;
+    if (used > peak) peak = used;
     return p;
   }
 };
@@ -974,7 +976,7 @@ __global__ void __launch_bounds__(BLR_NT, 1) k_factor(SchedParams P) {
   c.s = sm_carve(smem);
   c.status = P.status;
   DagShape d{P.p, P.q, P.off_larfb, P.off_tsqrt, P.off_tpmqrt};
-  TaskEnv env{&P, P.scratch + (size_t)blockIdx.x * P.slab, 0, false, nullptr, nullptr, &d, -1};
+  TaskEnv env{&P, P.scratch + (size_t)blockIdx.x * P.slab, 0, false, nullptr, nullptr, &d, -1, 0};
   constexpr bool kTensor = std::is_same<S, float>::value;
   static_assert(BLR_SMEM_BYTES >= TC_STAGE_BYTES && TC_STAGE_BYTES >= 3 * 128 * 128 * 4, "staging area");
   __shared__ uint64_t tc_bars[2];
@@ -1039,6 +1041,7 @@ __global__ void __launch_bounds__(BLR_NT, 1) k_factor(SchedParams P) {
         break;
     }
     if (env.overflow && threadIdx.x == 0) atomicOr(P.status, ST_RANK);
+    if (threadIdx.x == 0) atomicMax(P.slab_peak, (unsigned long long)env.peak);
     __threadfence();
     __syncthreads();
     if (threadIdx.x == 0 && type >= 0) {
