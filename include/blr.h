@@ -146,6 +146,14 @@ int blr_matrix_import(int m, int n, int b, const int* ranks_host, const double* 
                       blr_matrix** out, void* stream);
 
 /*
+ * blr_matrix_import_device -- as blr_matrix_import, with the tiles in device
+ * memory (tiles_dev, p*q*b*b doubles in the same layout; copied, not
+ * adopted).  ranks_host is host memory.
+ */
+int blr_matrix_import_device(int m, int n, int b, const int* ranks_host, const double* tiles_dev,
+                             blr_matrix** out, void* stream);
+
+/*
  * blr_matrix_export -- copy tiles and ranks of a matrix, or of a factor's
  * in-place storage, to host buffers of p*q*b*b doubles and p*q ints (same
  * layout as blr_matrix_import).  handle_is_factor selects the handle type.
@@ -214,6 +222,36 @@ int blr_apply_qt_noalloc(const blr_factor* f, double* b_dev, int ldb, int nrhs, 
  */
 int blr_lstsq(const blr_factor* f, const blr_matrix* a_orig, const double* b_dev, int ldb,
               double* x_dev, int ldx, int nrhs, int refine_steps, void* stream);
+
+/*
+ * blr_solve_r -- X = R^{-1} C (trans = 0, back substitution) or X = R^{-T} C
+ * (trans = 1, forward substitution) with the factor's n x n upper triangular
+ * BLR R (C, X device n x nrhs).  Errors: BLR_ERR_NUMERIC for a zero or
+ * non-finite diagonal entry of R.
+ */
+int blr_solve_r(const blr_factor* f, const double* c_dev, int ldc, double* x_dev, int ldx, int nrhs, int trans,
+                void* stream);
+
+/*
+ * blr_lstsq_backward -- adjoint of x = argmin ||A~ x - B||_F (the least
+ * squares use of A = QR, Section 1) for a loss L(x): given xbar = dL/dx
+ * (device n x nrhs) and the forward's B (m x nrhs) and x (n x nrhs), with
+ * z = (A~^T A~)^{-1} xbar = R^{-1} R^{-T} xbar (the stored R of f) and
+ * r = B - A~ x (A~ = a_orig, the matrix that was factored):
+ *   bbar = dL/dB = A~ z                              (device m x nrhs, ldbb)
+ *   dL/dA~ = r z^T - (A~ z) x^T, projected on the storage of a_orig:
+ *   grad_tiles (device, p*q*b*b doubles, the tile layout of
+ *   blr_matrix_import) receives for a dense tile (i,j) the b x b block of
+ *   dL/dA~, and for a low-rank tile U V^T the gradients dL/dU = (dL/dA~)_ij V
+ *   in its U slot and dL/dV = (dL/dA~)_ij^T U in its V slot; the rest of
+ *   each tile is zero.
+ * Every product runs on the device (triangular solves with the factor, BLR
+ * matrix products, one CTA per tile for the projection).
+ * Errors: BLR_ERR_INVALID (shapes), BLR_ERR_NUMERIC, BLR_ERR_OOM, BLR_ERR_CUDA.
+ */
+int blr_lstsq_backward(const blr_factor* f, const blr_matrix* a_orig, const double* b_dev, int ldb,
+                       const double* x_dev, int ldx, const double* xbar_dev, int ldxb, int nrhs,
+                       double* bbar_dev, int ldbb, double* grad_tiles_dev, void* stream);
 
 /* Y = A~ X for a BLR matrix (X device n x nrhs, Y device m x nrhs). */
 int blr_matmul(const blr_matrix* a, const double* x_dev, int ldx, double* y_dev, int ldy,

@@ -60,6 +60,7 @@ _SIGS = {
     "blr_compress_kernel": (_I, [_DP, _DP, _I, _I, _I, _I, _DP, ctypes.POINTER(Opts), ctypes.POINTER(_P), _P]),
     "blr_compress_dense": (_I, [_P, _I, _I, _I, ctypes.POINTER(Opts), ctypes.POINTER(_P), _P]),
     "blr_matrix_import": (_I, [_I, _I, _I, _IP, _DP, ctypes.POINTER(_P), _P]),
+    "blr_matrix_import_device": (_I, [_I, _I, _I, _IP, _P, ctypes.POINTER(_P), _P]),
     "blr_matrix_export": (_I, [_P, _I, _IP, _DP, _P]),
     "blr_matrix_clone": (_I, [_P, ctypes.POINTER(_P), _P]),
     "blr_qr": (_I, [_P, ctypes.POINTER(Opts), ctypes.POINTER(_P), _P]),
@@ -68,6 +69,8 @@ _SIGS = {
     "blr_lstsq": (_I, [_P, _P, _P, _I, _P, _I, _I, _I, _P]),
     "blr_matmul": (_I, [_P, _P, _I, _P, _I, _I, _P]),
     "blr_apply_r": (_I, [_P, _P, _I, _P, _I, _I, _P]),
+    "blr_solve_r": (_I, [_P, _P, _I, _P, _I, _I, _I, _P]),
+    "blr_lstsq_backward": (_I, [_P, _P, _P, _I, _P, _I, _P, _I, _I, _P, _I, _P, _P]),
     "blr_factor_export_t": (_I, [_P, _DP, _P]),
     "blr_stats": (_I, [_P, _I, ctypes.POINTER(Stats)]),
     "blr_destroy_matrix": (None, [_P]),
@@ -220,6 +223,19 @@ def blr_matrix_import(m: int, n: int, b: int, ranks: np.ndarray, tiles: np.ndarr
     return Matrix(h, m, n, b)
 
 
+def blr_matrix_import_device(m: int, n: int, b: int, ranks: np.ndarray, tiles, stream=None) -> Matrix:
+    """As blr_matrix_import with tiles a float64 CUDA tensor of p*q*b*b elements."""
+    r = np.ascontiguousarray(ranks, dtype=np.int32)
+    if tiles.dtype != __import__("torch").float64 or not tiles.is_cuda or not tiles.is_contiguous():
+        raise TypeError("tiles must be a contiguous float64 CUDA tensor")
+    if tiles.numel() != (m // b) * (n // b) * b * b:
+        raise ValueError("tiles has the wrong size")
+    h = ctypes.c_void_p()
+    _check(lib().blr_matrix_import_device(m, n, b, r.ctypes.data_as(_IP), ctypes.c_void_p(tiles.data_ptr()),
+                                          ctypes.byref(h), _stream(stream)))
+    return Matrix(h, m, n, b)
+
+
 def blr_matrix_export(obj, stream=None) -> tuple[np.ndarray, np.ndarray]:
     """(ranks (p*q,), tiles (p*q*b*b,)) of a Matrix or the in-place storage of a Factor."""
     p, q, b = obj.p, obj.q, obj.b
@@ -279,6 +295,27 @@ def blr_apply_r(f: Factor, x, stream=None):
     _check(lib().blr_apply_r(f.handle, ctypes.c_void_p(x.data_ptr()), _ld(x), ctypes.c_void_p(y.data_ptr()),
                              _ld(y), x.shape[1], _stream(stream)))
     return y
+
+
+def blr_solve_r(f: Factor, c, trans: int = 0, stream=None):
+    """X = R^{-1} C (trans=0) or R^{-T} C (trans=1); C column-major n x nrhs."""
+    x = fortran_empty(f.n, c.shape[1])
+    _check(lib().blr_solve_r(f.handle, ctypes.c_void_p(c.data_ptr()), _ld(c), ctypes.c_void_p(x.data_ptr()),
+                             _ld(x), c.shape[1], trans, _stream(stream)))
+    return x
+
+
+def blr_lstsq_backward(f: Factor, a_orig: Matrix, bmat, x, xbar, stream=None):
+    """(dL/dB (m x nrhs), dL/dtiles (p*q*b*b)) for x = argmin ||A~ x - B||."""
+    import torch
+    nrhs = bmat.shape[1]
+    bbar = fortran_empty(f.m, nrhs)
+    grad = torch.empty(a_orig.p * a_orig.q * a_orig.b * a_orig.b, dtype=torch.float64, device=bmat.device)
+    _check(lib().blr_lstsq_backward(f.handle, a_orig.handle, ctypes.c_void_p(bmat.data_ptr()), _ld(bmat),
+                                    ctypes.c_void_p(x.data_ptr()), _ld(x), ctypes.c_void_p(xbar.data_ptr()),
+                                    _ld(xbar), nrhs, ctypes.c_void_p(bbar.data_ptr()), _ld(bbar),
+                                    ctypes.c_void_p(grad.data_ptr()), _stream(stream)))
+    return bbar, grad
 
 
 def blr_factor_export_t(f: Factor, stream=None) -> np.ndarray:

@@ -162,8 +162,8 @@ extern "C" int blr_compress_dense(const double* a_dev, int lda, int m, int n, co
   return BLR_OK;
 }
 
-extern "C" int blr_matrix_import(int m, int n, int b, const int* ranks_host, const double* tiles_host,
-                                 blr_matrix** out, void* stream) {
+static int import_tiles(int m, int n, int b, const int* ranks_host, const double* tiles_host, cudaMemcpyKind kind,
+                        blr_matrix** out, void* stream) {
   int rc;
   if (!out || !ranks_host || !tiles_host) { blr_set_error("NULL argument"); return BLR_ERR_INVALID; }
   *out = nullptr;
@@ -179,12 +179,22 @@ extern "C" int blr_matrix_import(int m, int n, int b, const int* ranks_host, con
   blr_matrix* a = new blr_matrix;
   if ((rc = alloc_matrix(a, m, n, b))) { delete a; return rc; }
   cudaStream_t st = (cudaStream_t)stream;
-  rc = blr_cuda_check(cudaMemcpyAsync(a->tiles, tiles_host, sizeof(double) * (size_t)p * q * b * b, cudaMemcpyHostToDevice, st), "import tiles");
+  rc = blr_cuda_check(cudaMemcpyAsync(a->tiles, tiles_host, sizeof(double) * (size_t)p * q * b * b, kind, st), "import tiles");
   if (!rc) rc = blr_cuda_check(cudaMemcpyAsync(a->rank, ranks_host, sizeof(int) * p * q, cudaMemcpyHostToDevice, st), "import ranks");
   if (!rc) rc = blr_cuda_check(cudaStreamSynchronize(st), "import");
   if (rc) { free_matrix_storage(a); delete a; return rc; }
   *out = a;
   return BLR_OK;
+}
+
+extern "C" int blr_matrix_import(int m, int n, int b, const int* ranks_host, const double* tiles_host,
+                                 blr_matrix** out, void* stream) {
+  return import_tiles(m, n, b, ranks_host, tiles_host, cudaMemcpyHostToDevice, out, stream);
+}
+
+extern "C" int blr_matrix_import_device(int m, int n, int b, const int* ranks_host, const double* tiles_dev,
+                                        blr_matrix** out, void* stream) {
+  return import_tiles(m, n, b, ranks_host, tiles_dev, cudaMemcpyDeviceToDevice, out, stream);
 }
 
 extern "C" int blr_matrix_export(const void* handle, int handle_is_factor, int* ranks_host,

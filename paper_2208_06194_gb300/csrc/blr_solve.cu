@@ -55,14 +55,14 @@ __device__ void apply_ts_tile(const FactorView& F, int i, int k, double* Ck, dou
 }
 
 __global__ void __launch_bounds__(BLR_NT, 1) k_apply_q(FactorView F, double* B, long long ldb, int nrhs,
-                                                        int trans) {
+                                                        int trans, int cpc) {
   extern __shared__ double smem[];
   Ctx c;
   c.s = sm_carve(smem);
   c.status = F.status;
   c.fma = 0.0;
-  const int c0 = blockIdx.x * kColsPerCta;
-  const int nc = min(kColsPerCta, nrhs - c0);
+  const int c0 = blockIdx.x * cpc;
+  const int nc = min(cpc, nrhs - c0);
   if (nc <= 0) return;
   double* Bc = B + (size_t)c0 * ldb;
   double* scr = F.scratch + (size_t)blockIdx.x * F.slab;
@@ -84,19 +84,19 @@ __global__ void __launch_bounds__(BLR_NT, 1) k_apply_q(FactorView F, double* B, 
 
 // X = R^{-1} C (n x nrhs), back substitution by block rows.
 __global__ void __launch_bounds__(BLR_NT, 1) k_solve_r(FactorView F, const double* C, long long ldc,
-                                                        double* X, long long ldx, int nrhs) {
+                                                        double* X, long long ldx, int nrhs, int cpc) {
   extern __shared__ double smem[];
   Ctx c;
   c.s = sm_carve(smem);
   c.status = F.status;
   c.fma = 0.0;
-  const int c0 = blockIdx.x * kColsPerCta;
-  const int nc = min(kColsPerCta, nrhs - c0);
+  const int c0 = blockIdx.x * cpc;
+  const int nc = min(cpc, nrhs - c0);
   if (nc <= 0) return;
   const int b = F.b;
   double* scr = F.scratch + (size_t)blockIdx.x * F.slab;
   double* rhs = scr;                              // b x nc
-  double* tmp = scr + (size_t)b * kColsPerCta;    // cap x nc
+  double* tmp = scr + (size_t)b * cpc;            // cap x nc
   double* xs = c.s.vec;                           // nc values of the current row
   for (int k = F.q - 1; k >= 0; k--) {
     copy_mat(rhs, b, C + (size_t)k * b + (size_t)c0 * ldc, ldc, b, nc);
@@ -129,6 +129,117 @@ __global__ void __launch_bounds__(BLR_NT, 1) k_solve_r(FactorView F, const doubl
     }
     copy_mat(X + (size_t)k * b + (size_t)c0 * ldx, ldx, rhs, b, b, nc);
     __syncthreads();
+  }
+}
+
+// X = R^{-T} C (n x nrhs), forward substitution by block columns of R:
+// (R^T)_{kj} = R_jk^T for j <= k, so X_k = R_kk^{-T} (C_k - sum_{j<k} R_jk^T X_j).
+__global__ void __launch_bounds__(BLR_NT, 1) k_solve_rt(FactorView F, const double* C, long long ldc,
+                                                         double* X, long long ldx, int nrhs, int cpc) {
+  extern __shared__ double smem[];
+  Ctx c;
+  c.s = sm_carve(smem);
+  c.status = F.status;
+  c.fma = 0.0;
+  const int c0 = blockIdx.x * cpc;
+  const int nc = min(cpc, nrhs - c0);
+  if (nc <= 0) return;
+  const int b = F.b;
+  double* scr = F.scratch + (size_t)blockIdx.x * F.slab;
+  double* rhs = scr;                              // b x nc
+  double* tmp = scr + (size_t)b * cpc;            // cap x nc
+  double* xs = c.s.vec;
+  for (int k = 0; k < F.q; k++) {
+    copy_mat(rhs, b, C + (size_t)k * b + (size_t)c0 * ldc, ldc, b, nc);
+    __syncthreads();
+    for (int j = 0; j < k; j++) {
+      const double* Rjk = ftile(F, j, k);
+      const int r = __ldcg(F.rank + (size_t)k * F.p + j);
+      const double* Xj = X + (size_t)j * b + (size_t)c0 * ldx;
+      if (r < 0) {
+        gemm(b, nc, b, -1.0, Rjk, b, true, Xj, ldx, false, 1.0, rhs, b, c);
+      } else if (r > 0) {
+        // (U V^T)^T X_j = V (U^T X_j)
+        gemm(r, nc, b, 1.0, Rjk, b, true, Xj, ldx, false, 0.0, tmp, r, c);
+        gemm(b, nc, r, -1.0, Rjk + (size_t)b * F.cap, b, false, tmp, r, false, 1.0, rhs, b, c);
+      }
+    }
+    const double* Rkk = ftile(F, k, k);
+    for (int a = 0; a < b; a++) {
+      if (threadIdx.x < nc) {
+        const double d = __ldcg(Rkk + a + (size_t)a * b);
+        if (d == 0.0 || !isfinite(d)) atomicOr(F.status, ST_NUMERIC);
+        xs[threadIdx.x] = rhs[a + (size_t)threadIdx.x * b] / d;
+      }
+      __syncthreads();
+      const int rest = b - a - 1;
+      for (int e = threadIdx.x; e < rest * nc; e += BLR_NT) {
+        const int row = a + 1 + e % rest, col = e / rest;
+        rhs[row + (size_t)col * b] -= __ldcg(Rkk + a + (size_t)row * b) * xs[col];
+      }
+      if (threadIdx.x < nc) rhs[a + (size_t)threadIdx.x * b] = xs[threadIdx.x];
+      __syncthreads();
+    }
+    copy_mat(X + (size_t)k * b + (size_t)c0 * ldx, ldx, rhs, b, b, nc);
+    __syncthreads();
+  }
+}
+
+// Gradient of a loss through x = argmin ||A~ x - B|| with respect to the
+// storage of tile (i,j) of A~ (same layout as the tiles): with Abar =
+// r z^T - (A~ z) x^T (r = B - A~ x, z = (A~^T A~)^{-1} xbar), a dense tile
+// gets Abar_ij, a low-rank tile U V^T gets Ubar = Abar_ij V in its U slot and
+// Vbar = Abar_ij^T U in its V slot; the unused part of the tile is zero.
+// Each CTA handles tiles blockIdx.x, blockIdx.x + gridDim.x, ...
+__device__ void lstsq_grad_tile(const FactorView& A, int i, int j, const double* rres, long long ldr,
+                                const double* az, long long ldaz, const double* z, long long ldz, const double* x,
+                                long long ldxx, int nrhs, double* grad, double* scr, Ctx& c) {
+  const int b = A.b, cap = A.cap;
+  const double* T = ftile(A, i, j);
+  double* G = grad + ((size_t)j * A.p + i) * (size_t)b * b;
+  const int r = __ldcg(A.rank + (size_t)j * A.p + i);
+  const double* ri = rres + (size_t)i * b;
+  const double* ai = az + (size_t)i * b;
+  const double* zj = z + (size_t)j * b;
+  const double* xj = x + (size_t)j * b;
+  zero_mat(G, b, b, b);
+  __syncthreads();
+  if (r < 0) {
+    gemm(b, b, nrhs, 1.0, ri, ldr, false, zj, ldz, true, 0.0, G, b, c);
+    gemm(b, b, nrhs, -1.0, ai, ldaz, false, xj, ldxx, true, 1.0, G, b, c);
+    return;
+  }
+  if (r == 0) return;
+  double* s1 = scr;                         // V^T z_j  (r x nrhs)
+  double* s2 = s1 + (size_t)cap * nrhs;     // V^T x_j
+  double* t1 = s2 + (size_t)cap * nrhs;     // U^T r_i
+  double* t2 = t1 + (size_t)cap * nrhs;     // U^T (A z)_i
+  const double* U = T;
+  const double* V = T + (size_t)b * cap;
+  gemm(r, nrhs, b, 1.0, V, b, true, zj, ldz, false, 0.0, s1, r, c);
+  gemm(r, nrhs, b, 1.0, V, b, true, xj, ldxx, false, 0.0, s2, r, c);
+  gemm(r, nrhs, b, 1.0, U, b, true, ri, ldr, false, 0.0, t1, r, c);
+  gemm(r, nrhs, b, 1.0, U, b, true, ai, ldaz, false, 0.0, t2, r, c);
+  // Ubar = r_i s1^T - (A z)_i s2^T ; Vbar = z_j t1^T - x_j t2^T
+  gemm(b, r, nrhs, 1.0, ri, ldr, false, s1, r, true, 0.0, G, b, c);
+  gemm(b, r, nrhs, -1.0, ai, ldaz, false, s2, r, true, 1.0, G, b, c);
+  gemm(b, r, nrhs, 1.0, zj, ldz, false, t1, r, true, 0.0, G + (size_t)b * cap, b, c);
+  gemm(b, r, nrhs, -1.0, xj, ldxx, false, t2, r, true, 1.0, G + (size_t)b * cap, b, c);
+}
+
+__global__ void __launch_bounds__(BLR_NT, 1) k_lstsq_grad(FactorView A, const double* rres, long long ldr,
+                                                           const double* az, long long ldaz, const double* z,
+                                                           long long ldz, const double* x, long long ldxx, int nrhs,
+                                                           double* grad) {
+  extern __shared__ double smem[];
+  Ctx c;
+  c.s = sm_carve(smem);
+  c.status = A.status;
+  c.fma = 0.0;
+  double* scr = A.scratch + (size_t)blockIdx.x * A.slab;
+  for (int t = blockIdx.x; t < A.p * A.q; t += gridDim.x) {
+    __syncthreads();
+    lstsq_grad_tile(A, t % A.p, t / A.p, rres, ldr, az, ldaz, z, ldz, x, ldxx, nrhs, grad, scr, c);
   }
 }
 
@@ -232,18 +343,29 @@ int set_smem() {
   int rc = blr_cuda_check(cudaFuncSetAttribute(k_apply_q, cudaFuncAttributeMaxDynamicSharedMemorySize, BLR_SMEM_BYTES), "smem");
   if (!rc) rc = blr_cuda_check(cudaFuncSetAttribute(k_solve_r, cudaFuncAttributeMaxDynamicSharedMemorySize, BLR_SMEM_BYTES), "smem");
   if (!rc) rc = blr_cuda_check(cudaFuncSetAttribute(k_matmul, cudaFuncAttributeMaxDynamicSharedMemorySize, BLR_SMEM_BYTES), "smem");
+  if (!rc) rc = blr_cuda_check(cudaFuncSetAttribute(k_solve_rt, cudaFuncAttributeMaxDynamicSharedMemorySize, BLR_SMEM_BYTES), "smem");
+  if (!rc) rc = blr_cuda_check(cudaFuncSetAttribute(k_lstsq_grad, cudaFuncAttributeMaxDynamicSharedMemorySize, BLR_SMEM_BYTES), "smem");
   if (!rc) done = true;
   return rc;
+}
+
+// Right-hand-side columns per CTA: each CTA walks the whole reflector
+// sequence for its columns, so few columns should still fill the SMs.
+int cols_per_cta(int nrhs) {
+  const int nsm = blr_num_sms();
+  int cpc = (nrhs + nsm - 1) / nsm;
+  return cpc < 1 ? 1 : (cpc > kColsPerCta ? kColsPerCta : cpc);
 }
 
 int apply_q_launch(const blr_factor* f, double* B, int ldb, int nrhs, int trans, cudaStream_t st) {
   FactorView F{};
   Scratch S;
-  const int nct = (nrhs + kColsPerCta - 1) / kColsPerCta;
+  const int cpc = cols_per_cta(nrhs);
+  const int nct = (nrhs + cpc - 1) / cpc;
   int rc = set_smem();
-  if (!rc) rc = make_view(f->a, f->t, f->a.q, &F, &S, nct, (size_t)2 * f->a.cap * kColsPerCta + 64, st);
+  if (!rc) rc = make_view(f->a, f->t, f->a.q, &F, &S, nct, (size_t)2 * f->a.cap * cpc + 64, st);
   if (rc) return rc;
-  k_apply_q<<<nct, BLR_NT, BLR_SMEM_BYTES, st>>>(F, B, ldb, nrhs, trans);
+  k_apply_q<<<nct, BLR_NT, BLR_SMEM_BYTES, st>>>(F, B, ldb, nrhs, trans, cpc);
   rc = blr_cuda_check(cudaGetLastError(), "launch k_apply_q");
   if (rc) return rc;
   return finish(F, st, "blr_apply_qt");
@@ -252,14 +374,29 @@ int apply_q_launch(const blr_factor* f, double* B, int ldb, int nrhs, int trans,
 int solve_r_launch(const blr_factor* f, const double* C, int ldc, double* X, int ldx, int nrhs, cudaStream_t st) {
   FactorView F{};
   Scratch S;
-  const int nct = (nrhs + kColsPerCta - 1) / kColsPerCta;
+  const int cpc = cols_per_cta(nrhs);
+  const int nct = (nrhs + cpc - 1) / cpc;
   int rc = set_smem();
-  if (!rc) rc = make_view(f->a, f->t, 0, &F, &S, nct, (size_t)(f->a.b + f->a.cap) * kColsPerCta + 64, st);
+  if (!rc) rc = make_view(f->a, f->t, 0, &F, &S, nct, (size_t)(f->a.b + f->a.cap) * cpc + 64, st);
   if (rc) return rc;
-  k_solve_r<<<nct, BLR_NT, BLR_SMEM_BYTES, st>>>(F, C, ldc, X, ldx, nrhs);
+  k_solve_r<<<nct, BLR_NT, BLR_SMEM_BYTES, st>>>(F, C, ldc, X, ldx, nrhs, cpc);
   rc = blr_cuda_check(cudaGetLastError(), "launch k_solve_r");
   if (rc) return rc;
   return finish(F, st, "blr_lstsq");
+}
+
+int solve_rt_launch(const blr_factor* f, const double* C, int ldc, double* X, int ldx, int nrhs, cudaStream_t st) {
+  FactorView F{};
+  Scratch S;
+  const int cpc = cols_per_cta(nrhs);
+  const int nct = (nrhs + cpc - 1) / cpc;
+  int rc = set_smem();
+  if (!rc) rc = make_view(f->a, f->t, 0, &F, &S, nct, (size_t)(f->a.b + f->a.cap) * cpc + 64, st);
+  if (rc) return rc;
+  k_solve_rt<<<nct, BLR_NT, BLR_SMEM_BYTES, st>>>(F, C, ldc, X, ldx, nrhs, cpc);
+  rc = blr_cuda_check(cudaGetLastError(), "launch k_solve_rt");
+  if (rc) return rc;
+  return finish(F, st, "blr_solve_r");
 }
 
 int matmul_launch(const blr_matrix& a, int mode, const double* X, int ldx, double* Y, int ldy, int nrhs,
@@ -345,6 +482,72 @@ extern "C" int blr_lstsq(const blr_factor* f, const blr_matrix* a_orig, const do
   if (!rc) rc = blr_cuda_check(cudaStreamSynchronize(st), "blr_lstsq");
   if (cbuf) cudaFree(cbuf);
   if (dx) cudaFree(dx);
+  return rc;
+}
+
+
+extern "C" int blr_solve_r(const blr_factor* f, const double* c_dev, int ldc, double* x_dev, int ldx, int nrhs,
+                           int trans, void* stream) {
+  if (!f || !c_dev || !x_dev) { blr_set_error("NULL argument"); return BLR_ERR_INVALID; }
+  if (ldc < f->a.n || ldx < f->a.n || nrhs < 0) { blr_set_error("bad leading dimension"); return BLR_ERR_INVALID; }
+  if (nrhs == 0) return BLR_OK;
+  cudaStream_t st = (cudaStream_t)stream;
+  return trans ? solve_rt_launch(f, c_dev, ldc, x_dev, ldx, nrhs, st) : solve_r_launch(f, c_dev, ldc, x_dev, ldx, nrhs, st);
+}
+
+extern "C" int blr_lstsq_backward(const blr_factor* f, const blr_matrix* a_orig, const double* b_dev, int ldb,
+                                  const double* x_dev, int ldx, const double* xbar_dev, int ldxb, int nrhs,
+                                  double* bbar_dev, int ldbb, double* grad_tiles_dev, void* stream) {
+  if (!f || !a_orig || !b_dev || !x_dev || !xbar_dev || !bbar_dev || !grad_tiles_dev) {
+    blr_set_error("NULL argument");
+    return BLR_ERR_INVALID;
+  }
+  const int m = f->a.m, n = f->a.n;
+  if (a_orig->m != m || a_orig->n != n || a_orig->b != f->a.b) {
+    blr_set_error("the BLR matrix does not match the factor");
+    return BLR_ERR_INVALID;
+  }
+  if (ldb < m || ldx < n || ldxb < n || ldbb < m || nrhs < 0) { blr_set_error("bad leading dimension"); return BLR_ERR_INVALID; }
+  cudaStream_t st = (cudaStream_t)stream;
+  const blr_matrix& A = *a_orig;
+  if (nrhs == 0) {
+    return blr_cuda_check(cudaMemsetAsync(grad_tiles_dev, 0, sizeof(double) * (size_t)A.p * A.q * A.b * A.b, st),
+                          "clear gradient");
+  }
+  double *y = nullptr, *z = nullptr, *rr = nullptr;
+  int rc = blr_cuda_check(cudaMalloc(&y, sizeof(double) * (size_t)n * nrhs), "backward buffer");
+  if (!rc) rc = blr_cuda_check(cudaMalloc(&z, sizeof(double) * (size_t)n * nrhs), "backward buffer");
+  if (!rc) rc = blr_cuda_check(cudaMalloc(&rr, sizeof(double) * (size_t)m * nrhs), "backward buffer");
+  // z = (R^T R)^{-1} xbar = R^{-1} (R^{-T} xbar)
+  if (!rc) rc = solve_rt_launch(f, xbar_dev, ldxb, y, n, nrhs, st);
+  if (!rc) rc = solve_r_launch(f, y, n, z, n, nrhs, st);
+  // Bbar = A~ z
+  if (!rc) rc = matmul_launch(A, 0, z, n, bbar_dev, ldbb, nrhs, st);
+  // r = B - A~ x
+  if (!rc) rc = matmul_launch(A, 0, x_dev, ldx, rr, m, nrhs, st);
+  if (!rc) {
+    k_axpby<<<256, 256, 0, st>>>(rr, m, b_dev, ldb, m, nrhs, 1.0, -1.0);
+    rc = blr_cuda_check(cudaGetLastError(), "axpby");
+  }
+  if (!rc) {
+    FactorView F{};
+    Scratch S;
+    rc = set_smem();
+    int nct = 2 * blr_num_sms();
+    if (nct > A.p * A.q) nct = A.p * A.q;
+    if (!rc) rc = make_view(A, nullptr, 0, &F, &S, nct, (size_t)4 * A.cap * nrhs + 64, st);
+    if (!rc) {
+      // (A~ z) is read back from bbar_dev
+      k_lstsq_grad<<<nct, BLR_NT, BLR_SMEM_BYTES, st>>>(F, rr, m, bbar_dev, ldbb, z, n, x_dev, ldx, nrhs,
+                                                       grad_tiles_dev);
+      rc = blr_cuda_check(cudaGetLastError(), "launch k_lstsq_grad");
+    }
+    if (!rc) rc = finish(F, st, "blr_lstsq_backward");
+  }
+  if (!rc) rc = blr_cuda_check(cudaStreamSynchronize(st), "blr_lstsq_backward");
+  if (y) cudaFree(y);
+  if (z) cudaFree(z);
+  if (rr) cudaFree(rr);
   return rc;
 }
 
@@ -440,7 +643,7 @@ extern "C" int blr_apply_qt_noalloc(const blr_factor* f, double* b_dev, int ldb,
   k_fill_toff<<<1, 256, 0, st>>>(const_cast<long long*>(F.toff), a.p, a.q);
   rc = blr_cuda_check(cudaGetLastError(), "launch k_fill_toff");
   if (rc) return rc;
-  k_apply_q<<<nct, BLR_NT, BLR_SMEM_BYTES, st>>>(F, b_dev, ldb, nrhs, trans ? 0 : 1);
+  k_apply_q<<<nct, BLR_NT, BLR_SMEM_BYTES, st>>>(F, b_dev, ldb, nrhs, trans ? 0 : 1, kColsPerCta);
   rc = blr_cuda_check(cudaGetLastError(), "launch k_apply_q");
   if (rc) return rc;
   int s = 0;
