@@ -91,7 +91,13 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="mixed", choices=["fp64", "mixed"])
     ap.add_argument("--tol", type=float, default=1e-5)
-    ap.add_argument("--dense-rank", type=int, default=128)
+    # dense threshold per path (a low-rank result above it is stored dense):
+    # measured best at 65536 x 32768, tol 1e-5 (mixed: 8 4.38 s, 16 4.41, 32 4.85,
+    # 64 5.67, 128 8.63; FP64: 96 57.4 s, 128 51.0, 160 54.8).  The mixed path
+    # runs dense tiles on the tensor cores, low-rank ones as FP32 SIMT code;
+    # 32 = b/16 keeps the low-rank format where it still pays.
+    ap.add_argument("--dense-rank", type=int, default=0, help="0: 32 for mixed, 128 for fp64")
+    ap.add_argument("--dense-rank-fp64", type=int, default=128)
     ap.add_argument("--size", default="full", choices=list(SIZES))
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-e2e", action="store_true")
@@ -288,6 +294,8 @@ def workload_name(args):
 
 def main():
     args = parse()
+    if args.dense_rank == 0:
+        args.dense_rank = 32 if args.precision == "mixed" else 128
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", str(args.gpus)))
     local = int(os.environ.get("LOCAL_RANK", "0"))
@@ -316,8 +324,8 @@ def main():
             dist.barrier()
         torch.cuda.synchronize()
 
-    def one_step(o):
-        a = blr.blr_matrix_clone(a0)
+    def one_step(o, src=None):
+        a = blr.blr_matrix_clone(a0 if src is None else src)
         torch.cuda.synchronize()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
@@ -355,13 +363,16 @@ def main():
     fp64 = None
     if not args.no_compare_fp64 and prec == blr.BLR_PREC_MIXED and world == 1:
         o64 = blr.blr_opts_default(b=s["b"], tol=args.tol, precision=blr.BLR_PREC_FP64,
-                                   dense_rank=args.dense_rank, scratch_b2=args.scratch_b2)
-        f64, t64 = one_step(o64)
-        r64 = probes(blr, f64, a0, pr, torch, dev)
+                                   dense_rank=args.dense_rank_fp64, scratch_b2=args.scratch_b2)
+        a64 = blr.blr_compress_kernel(pr.x, pr.y, "yukawa3d", o64)    # its own dense threshold
+        f64, t64 = one_step(o64, a64)
+        r64 = probes(blr, f64, a64, pr, torch, dev)
         st64 = blr.blr_stats(f64)
+        a64.destroy()
         fp64 = {"seconds": t64, "res_A": r64[0], "res_At": r64[1], "orth": r64[2],
                 "gflops_counted": st64["flops"][4] / 1e9,
-                "meets_10tol": bool(r64[0] <= 10 * args.tol), "mixed_speedup": t64 / t_step}
+                "meets_10tol": bool(r64[0] <= 10 * args.tol), "mixed_speedup": t64 / t_step,
+                "dense_rank": args.dense_rank_fp64}
         f64.destroy()
 
     # end to end through host buffers: import (H2D) + blr_qr + export (D2H)

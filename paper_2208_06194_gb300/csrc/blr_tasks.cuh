@@ -23,11 +23,19 @@
     __syncthreads();                                                             \
     if (threadIdx.x == 0) atomicAdd(env.P->phase + (id), tc_gtimer() - ph_t0_); \
   } while (0)
+#define PH_BEGIN()                       \
+  __syncthreads();                       \
+  const unsigned long long ph_b0_ = tc_gtimer();
+#define PH_END(id)                                                               \
+  __syncthreads();                                                               \
+  if (threadIdx.x == 0) atomicAdd(env.P->phase + (id), tc_gtimer() - ph_b0_);
 #else
 #define PH(id, ...) \
   do {              \
     __VA_ARGS__;    \
   } while (0)
+#define PH_BEGIN()
+#define PH_END(id)
 #endif
 
 namespace {
@@ -374,7 +382,7 @@ __device__ void tc_apply_prepared(TaskEnv& env, const float* slot, double* Ct, d
   float* cc_l = (float*)env.alloc(op / 2);
   float* zc_h = (float*)env.alloc(op / 2);    // Z as an operand (rows = columns n, K = reflectors)
   float* zc_l = (float*)env.alloc(op / 2);
-  tc_canon(cc_h, cc_l, Rp, b, (const double*)Cb, b, 1, b, b);    // (n, r) = Cb[r + n b]
+  PH(12, tc_canon(cc_h, cc_l, Rp, b, (const double*)Cb, b, 1, b, b));    // (n, r) = Cb[r + n b]
   fence_async_global();
   __syncthreads();
   const int nchunk = b / TC_KC;
@@ -382,11 +390,13 @@ __device__ void tc_apply_prepared(TaskEnv& env, const float* slot, double* Ct, d
   for (int m0 = 0; m0 < b; m0 += TC_M) {
     for (int n0 = 0; n0 < b; n0 += 256) {
       const int nn = min(256, b - n0), nn16 = (nn + 15) & ~15;
-      tc_gemm_bulk(tc, q, n0, yt_h + (size_t)m0 * TC_KC, yt_l + (size_t)m0 * TC_KC, cs, cc_h + (size_t)n0 * TC_KC,
-                   cc_l + (size_t)n0 * TC_KC, cs, nn16, nchunk);
+      PH(13, tc_gemm_bulk(tc, q, n0, yt_h + (size_t)m0 * TC_KC, yt_l + (size_t)m0 * TC_KC, cs, cc_h + (size_t)n0 * TC_KC,
+                   cc_l + (size_t)n0 * TC_KC, cs, nn16, nchunk));
     }
     for (int n0 = 0; n0 < b; n0 += 256) {
       const int nn = min(256, b - n0), nn16 = (nn + 15) & ~15;
+      {
+      PH_BEGIN();
       tc_epilogue16(tc, n0, nn16, [&](int r, int col, const float* v) {
         const int a = m0 + r;
         if (a >= b) return;
@@ -397,6 +407,8 @@ __device__ void tc_apply_prepared(TaskEnv& env, const float* slot, double* Ct, d
         for (int u = 0; u < 16; u++)
           if (col + u < nn) tc_canon_put(zc_h, zc_l, Rp, n0 + col + u, a, v[u] + (float)ct[u]);
       });
+      PH_END(14);
+      }
     }
   }
   fence_async_global();
@@ -406,11 +418,13 @@ __device__ void tc_apply_prepared(TaskEnv& env, const float* slot, double* Ct, d
     const int kch = min(b, m0 + TC_M) / TC_KC;
     for (int n0 = 0; n0 < b; n0 += 256) {
       const int nn = min(256, b - n0), nn16 = (nn + 15) & ~15;
-      tc_gemm_bulk(tc, q, n0, tt_h + (size_t)m0 * TC_KC, tt_l + (size_t)m0 * TC_KC, cs, zc_h + (size_t)n0 * TC_KC,
-                   zc_l + (size_t)n0 * TC_KC, cs, nn16, kch);
+      PH(13, tc_gemm_bulk(tc, q, n0, tt_h + (size_t)m0 * TC_KC, tt_l + (size_t)m0 * TC_KC, cs, zc_h + (size_t)n0 * TC_KC,
+                   zc_l + (size_t)n0 * TC_KC, cs, nn16, kch));
     }
     for (int n0 = 0; n0 < b; n0 += 256) {
       const int nn = min(256, b - n0), nn16 = (nn + 15) & ~15;
+      {
+      PH_BEGIN();
       tc_epilogue16(tc, n0, nn16, [&](int r, int col, const float* v) {
         const int a = m0 + r;
         if (a >= b) return;
@@ -425,6 +439,8 @@ __device__ void tc_apply_prepared(TaskEnv& env, const float* slot, double* Ct, d
           }
         }
       });
+      PH_END(14);
+      }
     }
   }
   fence_async_global();
@@ -433,11 +449,13 @@ __device__ void tc_apply_prepared(TaskEnv& env, const float* slot, double* Ct, d
   for (int m0 = 0; m0 < b; m0 += TC_M) {
     for (int n0 = 0; n0 < b; n0 += 256) {
       const int nn = min(256, b - n0), nn16 = (nn + 15) & ~15;
-      tc_gemm_bulk(tc, q, n0, yc_h + (size_t)m0 * TC_KC, yc_l + (size_t)m0 * TC_KC, cs, cc_h + (size_t)n0 * TC_KC,
-                   cc_l + (size_t)n0 * TC_KC, cs, nn16, nchunk);
+      PH(13, tc_gemm_bulk(tc, q, n0, yc_h + (size_t)m0 * TC_KC, yc_l + (size_t)m0 * TC_KC, cs, cc_h + (size_t)n0 * TC_KC,
+                   cc_l + (size_t)n0 * TC_KC, cs, nn16, nchunk));
     }
     for (int n0 = 0; n0 < b; n0 += 256) {
       const int nn = min(256, b - n0), nn16 = (nn + 15) & ~15;
+      {
+      PH_BEGIN();
       tc_epilogue16(tc, n0, nn16, [&](int r, int col, const float* v) {
         const int rr = m0 + r;
         if (rr >= b) return;
@@ -448,6 +466,8 @@ __device__ void tc_apply_prepared(TaskEnv& env, const float* slot, double* Ct, d
         for (int u = 0; u < 16; u++)
           if (col + u < nn) Cb[rr + (size_t)(n0 + col + u) * b] = cb[u] - (double)v[u];
       });
+      PH_END(14);
+      }
     }
   }
   c.fma += 2.0 * b * b * b + (double)b * b * b / 2;
@@ -836,11 +856,11 @@ __device__ void tpmqrt_tc_dense(TaskEnv& env, const double* Yt, const double* Ti
   double* Ad = At;
   if (rR >= 0) {
     Rd = env.alloc((size_t)b * b);
-    tc_densify(env, Rt, rR, Rd, c);
+    PH(15, tc_densify(env, Rt, rR, Rd, c));
   }
   if (rA >= 0) {
     Ad = env.alloc((size_t)b * b);
-    tc_densify(env, At, rA, Ad, c);
+    PH(15, tc_densify(env, At, rA, Ad, c));
   }
   if (prep) tc_apply_prepared(env, prep, Rd, Ad, c);
   else tc_apply_ts_dense(env, Yt, Tik, Rd, b, Ad, b, b, c);
