@@ -473,6 +473,10 @@ __device__ void tc_apply_prepared(TaskEnv& env, const float* slot, double* Ct, d
   c.fma += 2.0 * b * b * b + (double)b * b * b / 2;
 }
 
+__device__ void tc_apply_ts_group(TaskEnv& env, const double* Yg, long long ldy, int wg, const double* Tblk,
+                                  double* Ct, long long ldt, double* Cb, long long ldb, int nc, float* Tg,
+                                  float* Zs, Ctx& c);
+
 // TSQRT(i,k): QR([R_kk; A^V_ik]) with A^V = V^T (low-rank) or the dense tile
 // (Section 3.4.3, Eqs. 19-21); Y_ik overwrites A^V in place.  The panel
 // factorization is FP64; the update of the trailing columns runs in S.
@@ -491,9 +495,20 @@ __device__ void task_tsqrt(TaskEnv& env, int i, int k, Ctx& c) {
     __syncthreads();
     return;
   }
+  // mixed path, dense tail: the panels' updates reach only the columns of
+  // their 128-column group; each finished group updates the columns to its
+  // right on the tensor cores (whole-group T, tc_apply_ts_group)
+  const bool grouped = std::is_same<S, float>::value && r < 0 && env.tc != nullptr && b > 128;
+  float* gTg = nullptr;
+  float* gZs = nullptr;
+  if (grouped) {
+    gTg = (float*)env.alloc(128 * 128 / 2);
+    gZs = (float*)env.alloc((size_t)128 * b / 2);
+  }
   for (int c0 = 0; c0 < b; c0 += BLR_NB) {
     const int w = BLR_NB;
     const int ldb = ry | 1;
+    const int gend = grouped ? min(b, (c0 / 128 + 1) * 128) : b;   // end of this panel's update range
     __syncthreads();
     for (int e = threadIdx.x; e < w * w; e += BLR_NT) {
       int a = e % w, l = e / w;
@@ -511,17 +526,22 @@ __device__ void task_tsqrt(TaskEnv& env, int i, int k, Ctx& c) {
     }
     stage_out(Bp, c.s.pnl, ldb, ry, w);
     __syncthreads();
-    if (c0 + w < b) {
+    if (c0 + w < gend) {
       View<double> Cb = Bv.shifted(0, c0 + w);
       if (std::is_same<S, double>::value) {
-        apply_refl_ts(R + c0 + (size_t)(c0 + w) * b, b, Cb, ry, b - c0 - w, c.s.pnl, ldb, w, c.s.t, true, c);
+        apply_refl_ts(R + c0 + (size_t)(c0 + w) * b, b, Cb, ry, gend - c0 - w, c.s.pnl, ldb, w, c.s.t, true, c);
       } else {
         const int ldy = stage_reflector_panel<S>(Bv, ry, c0, w, Tk, c);
-        apply_refl_ts(R + c0 + (size_t)(c0 + w) * b, b, Cb, ry, b - c0 - w, (const S*)as<S>(c.s.pnl), ldy, w,
+        apply_refl_ts(R + c0 + (size_t)(c0 + w) * b, b, Cb, ry, gend - c0 - w, (const S*)as<S>(c.s.pnl), ldy, w,
                       (const S*)as<S>(c.s.t), true, c);
       }
     }
     __syncthreads();
+    if (grouped && c0 + w == gend && gend < b) {
+      const int g0 = gend - 128;
+      tc_apply_ts_group(env, B + (size_t)g0 * b, b, 128, Tk + (size_t)g0 * BLR_NB, R + g0 + (size_t)gend * b, b,
+                        B + (size_t)gend * b, b, b - gend, gTg, gZs, c);
+    }
   }
   if constexpr (std::is_same<S, float>::value) {
     if (r < 0 && P.prep && env.tc) {
@@ -776,73 +796,92 @@ __device__ void tc_group_t(const double* Tblk, int wg, const float* Gs, float* T
 //   Z = Ct(g rows) + Y_g^T Cb;  W = T_g^T Z;  Ct(g rows) -= W;  Cb -= Y_g W.
 // Products on the tensor cores (3xTF32, FP32 accumulation); the tiles stay
 // FP64 and receive FP64 updates.
-__device__ void tc_apply_ts_dense(TaskEnv& env, const double* Y, const double* Tik, double* Ct, long long ldt,
-                                  double* Cb, long long ldb, int nc, Ctx& c) {
+// One group of wg <= 128 consecutive reflectors [e_a; y_a] of a dense block
+// (tails Yg, b x wg, ld ldy; inner T blocks at Tblk) applied to [Ct; Cb] on
+// the tensor cores, Ct the wg rows of the top that the group's identity part
+// touches (ld ldt) and Cb the b x nc bottom (ld ldb):
+//   Z = Ct + Y_g^T Cb;  W = T_g^T Z;  Ct -= W;  Cb -= Y_g W
+// with T_g assembled from the inner blocks and G = Y_g^T Y_g.  Tg (128 x 128)
+// and Zs (128 x nc) are global scratch.
+__device__ void tc_apply_ts_group(TaskEnv& env, const double* Yg, long long ldy, int wg, const double* Tblk,
+                                  double* Ct, long long ldt, double* Cb, long long ldb, int nc, float* Tg,
+                                  float* Zs, Ctx& c) {
   TcCtx& tc = *env.tc;
   const int b = env.P->b;
-  float* Tg = (float*)env.alloc(128 * 128 / 2);          // global copy of T_g (A operand of W)
-  float* Zs = (float*)env.alloc((size_t)128 * nc / 2);   // Z, then W (ld 128)
   float* Gsm = tc.buf;                                   // staging area, idle between products
   float* Tsm = tc.buf + 128 * 128;
   float* Xsm = tc.buf + 2 * 128 * 128;
+  // G = Y_g^T Y_g
+  tc_gemm_tile(tc, 0, Yg, ldy, 1, wg, Yg, ldy, 1, wg, wg, b);
+  tc_epilogue(tc, 0, wg, [&](int r, int col, float v) { Gsm[r + col * 128] = v; });
+  c.fma += (double)wg * wg * b / 2;
+  tc_group_t(Tblk, wg, Gsm, Tsm, Xsm, c);
+  for (int e = threadIdx.x; e < 128 * 128; e += BLR_NT) Tg[e] = Tsm[e];
+  __syncthreads();
+  // Z = Ct + Y_g^T Cb
+  for (int n0 = 0; n0 < nc; n0 += 256) {
+    const int nn = min(256, nc - n0), nn16 = (nn + 15) & ~15;
+    tc_gemm_tile(tc, n0, Yg, ldy, 1, wg, Cb + (size_t)n0 * ldb, ldb, 1, nn, nn16, b);
+  }
+  for (int n0 = 0; n0 < nc; n0 += 256) {
+    const int nn = min(256, nc - n0), nn16 = (nn + 15) & ~15;
+    tc_epilogue(tc, n0, nn16, [&](int r, int col, float v) {
+      if (r < wg && col < nn) {
+        const size_t n = n0 + col;
+        Zs[r + n * 128] = v + (float)ldg(Ct + r + n * ldt);
+      }
+    });
+  }
+  // W = T_g^T Z; Ct -= W
+  for (int n0 = 0; n0 < nc; n0 += 256) {
+    const int nn = min(256, nc - n0), nn16 = (nn + 15) & ~15;
+    tc_gemm_tile(tc, n0, (const float*)Tg, 128, 1, wg, (const float*)Zs + (size_t)n0 * 128, 128, 1, nn, nn16, wg);
+  }
+  for (int n0 = 0; n0 < nc; n0 += 256) {
+    const int nn = min(256, nc - n0), nn16 = (nn + 15) & ~15;
+    tc_epilogue(tc, n0, nn16, [&](int r, int col, float v) {
+      if (r < wg && col < nn) {
+        const size_t n = n0 + col;
+        double* p = Ct + r + n * ldt;
+        *p = ldg(p) - (double)v;
+        Zs[r + n * 128] = v;
+      }
+    });
+  }
+  // Cb -= Y_g W
+  for (int r0 = 0; r0 < b; r0 += TC_M) {
+    const int mrow = min(TC_M, b - r0);
+    for (int n0 = 0; n0 < nc; n0 += 256) {
+      const int nn = min(256, nc - n0), nn16 = (nn + 15) & ~15;
+      tc_gemm_tile(tc, n0, Yg + r0, 1, ldy, mrow, (const float*)Zs + (size_t)n0 * 128, 128, 1, nn, nn16, wg);
+    }
+    for (int n0 = 0; n0 < nc; n0 += 256) {
+      const int nn = min(256, nc - n0), nn16 = (nn + 15) & ~15;
+      tc_epilogue(tc, n0, nn16, [&](int r, int col, float v) {
+        if (r < mrow && col < nn) {
+          double* p = Cb + (r0 + r) + (size_t)(n0 + col) * ldb;
+          *p = ldg(p) - (double)v;
+        }
+      });
+    }
+  }
+  c.fma += (double)wg * nc * b + (double)wg * nc * wg / 2 + (double)b * nc * wg;
+}
+
+// [Ct (b x nc, ld ldt); Cb (b x nc, ld ldb)] <- Q^T [Ct; Cb] for the dense
+// reflector block of a TSQRT, Q = I - [I; Y] T [I; Y]^T with Y b x b dense
+// (Section 3.4.4, Eq. 21), in groups of 128 reflectors.  Products on the
+// tensor cores (3xTF32, FP32 accumulation); the tiles stay FP64 and receive
+// FP64 updates.
+__device__ void tc_apply_ts_dense(TaskEnv& env, const double* Y, const double* Tik, double* Ct, long long ldt,
+                                  double* Cb, long long ldb, int nc, Ctx& c) {
+  const int b = env.P->b;
+  float* Tg = (float*)env.alloc(128 * 128 / 2);          // global copy of T_g (A operand of W)
+  float* Zs = (float*)env.alloc((size_t)128 * nc / 2);   // Z, then W (ld 128)
   for (int c0 = 0; c0 < b; c0 += 128) {
     const int wg = min(128, b - c0);
-    const double* Yg = Y + (size_t)c0 * b;
-    // G = Y_g^T Y_g
-    tc_gemm_tile(tc, 0, Yg, b, 1, wg, Yg, b, 1, wg, wg, b);
-    tc_epilogue(tc, 0, wg, [&](int r, int col, float v) { Gsm[r + col * 128] = v; });
-    c.fma += (double)wg * wg * b / 2;
-    tc_group_t(Tik + (size_t)c0 * BLR_NB, wg, Gsm, Tsm, Xsm, c);
-    for (int e = threadIdx.x; e < 128 * 128; e += BLR_NT) Tg[e] = Tsm[e];
-    __syncthreads();
-    // Z = Ct(c0 : c0 + wg, :) + Y_g^T Cb
-    for (int n0 = 0; n0 < nc; n0 += 256) {
-      const int nn = min(256, nc - n0), nn16 = (nn + 15) & ~15;
-      tc_gemm_tile(tc, n0, Yg, b, 1, wg, Cb + (size_t)n0 * ldb, ldb, 1, nn, nn16, b);
-    }
-    for (int n0 = 0; n0 < nc; n0 += 256) {
-      const int nn = min(256, nc - n0), nn16 = (nn + 15) & ~15;
-      tc_epilogue(tc, n0, nn16, [&](int r, int col, float v) {
-        if (r < wg && col < nn) {
-          const size_t n = n0 + col;
-          Zs[r + n * 128] = v + (float)ldg(Ct + (c0 + r) + n * ldt);
-        }
-      });
-    }
-    // W = T_g^T Z; Ct(c0 : c0 + wg, :) -= W
-    for (int n0 = 0; n0 < nc; n0 += 256) {
-      const int nn = min(256, nc - n0), nn16 = (nn + 15) & ~15;
-      tc_gemm_tile(tc, n0, (const float*)Tg, 128, 1, wg, (const float*)Zs + (size_t)n0 * 128, 128, 1, nn, nn16, wg);
-    }
-    for (int n0 = 0; n0 < nc; n0 += 256) {
-      const int nn = min(256, nc - n0), nn16 = (nn + 15) & ~15;
-      tc_epilogue(tc, n0, nn16, [&](int r, int col, float v) {
-        if (r < wg && col < nn) {
-          const size_t n = n0 + col;
-          double* p = Ct + (c0 + r) + n * ldt;
-          *p = ldg(p) - (double)v;
-          Zs[r + n * 128] = v;
-        }
-      });
-    }
-    // Cb -= Y_g W
-    for (int r0 = 0; r0 < b; r0 += TC_M) {
-      const int mrow = min(TC_M, b - r0);
-      for (int n0 = 0; n0 < nc; n0 += 256) {
-        const int nn = min(256, nc - n0), nn16 = (nn + 15) & ~15;
-        tc_gemm_tile(tc, n0, Yg + r0, 1, b, mrow, (const float*)Zs + (size_t)n0 * 128, 128, 1, nn, nn16, wg);
-      }
-      for (int n0 = 0; n0 < nc; n0 += 256) {
-        const int nn = min(256, nc - n0), nn16 = (nn + 15) & ~15;
-        tc_epilogue(tc, n0, nn16, [&](int r, int col, float v) {
-          if (r < mrow && col < nn) {
-            double* p = Cb + (r0 + r) + (size_t)(n0 + col) * ldb;
-            *p = ldg(p) - (double)v;
-          }
-        });
-      }
-    }
-    c.fma += (double)wg * nc * b + (double)wg * nc * wg / 2 + (double)b * nc * wg;
+    tc_apply_ts_group(env, Y + (size_t)c0 * b, b, wg, Tik + (size_t)c0 * BLR_NB, Ct + c0, ldt, Cb, ldb, nc, Tg, Zs,
+                      c);
   }
 }
 

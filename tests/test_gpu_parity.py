@@ -246,7 +246,12 @@ def test_invalid_arguments_fail_loudly(lib):
 # Orth <= 1e-6 (the mixed-precision target), Res <= 10 x the recompression
 # tolerance, R within 1e-5 of the FP64 oracle on well-conditioned inputs.
 
-@pytest.mark.parametrize("m,n,b,seed,dense,zero", CASES[:4])
+MIXED_CASES = CASES[:4] + [
+    (1024, 512, 256, 6, ((2, 0), (3, 1)), ()),      # b > 128: grouped tensor-core TSQRT updates
+]
+
+
+@pytest.mark.parametrize("m,n,b,seed,dense,zero", MIXED_CASES)
 def test_mixed_precision_factor_close_to_oracle(lib, m, n, b, seed, dense, zero):
     import torch
     a = _mixed_blr(m, n, b, seed, dense, zero)
