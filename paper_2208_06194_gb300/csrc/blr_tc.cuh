@@ -290,33 +290,40 @@ __device__ __forceinline__ size_t canon_index(int R, int r, int k) {
 template <class G>
 __device__ void tc_canon(float* hi, float* lo, int R, int K, const G* src, long long sr, long long sc, int nrow,
                          int kvalid) {
-  const long long groups = (long long)R * (K / 4);
-  if (sc == 1) {
-    for (long long e = threadIdx.x; e < groups; e += BLR_NT) {
-      const int r8 = (int)(e & 7), kq = (int)((e >> 3) % (K / 4)), rg = (int)(e / (8LL * (K / 4)));
-      const int r = rg * 8 + r8, k = kq * 4;
-      float h[4], l[4];
+  // four (row, 4-column) groups per thread per pass, all loads issued first
+  constexpr int U = 4;
+  const int kq4 = K / 4;
+  const int groups = R * kq4;
+  for (int base = 0; base < groups; base += BLR_NT * U) {
+    G v[U][4];
+    int rr[U], kk[U];
+#pragma unroll
+    for (int u = 0; u < U; u++) {
+      const int e = base + u * BLR_NT + threadIdx.x;
+      int r, k;
+      if (sc == 1) {   // eight consecutive threads: eight rows of one 4-column group
+        const int r8 = e & 7, kq = (e >> 3) % kq4, rg = (e >> 3) / kq4;
+        r = rg * 8 + r8;
+        k = kq * 4;
+      } else {         // consecutive threads: consecutive rows
+        r = e % R;
+        k = (e / R) * 4;
+      }
+      rr[u] = r;
+      kk[u] = k;
 #pragma unroll
       for (int i = 0; i < 4; i++) {
-        G v = G(0);
-        if (r < nrow && k + i < kvalid) v = tc_ld(src + (long long)r * sr + (k + i));
-        tc_split((float)v, h[i], l[i]);
+        v[u][i] = G(0);
+        if (e < groups && r < nrow && k + i < kvalid) v[u][i] = tc_ld(src + (long long)r * sr + (long long)(k + i) * sc);
       }
-      const size_t off = canon_index(R, r, k);
-      *reinterpret_cast<float4*>(hi + off) = make_float4(h[0], h[1], h[2], h[3]);
-      *reinterpret_cast<float4*>(lo + off) = make_float4(l[0], l[1], l[2], l[3]);
     }
-  } else {
-    for (long long e = threadIdx.x; e < groups; e += BLR_NT) {
-      const int r = (int)(e % R), k = (int)(e / R) * 4;
+#pragma unroll
+    for (int u = 0; u < U; u++) {
+      if (base + u * BLR_NT + (int)threadIdx.x >= groups) continue;
       float h[4], l[4];
 #pragma unroll
-      for (int i = 0; i < 4; i++) {
-        G v = G(0);
-        if (r < nrow && k + i < kvalid) v = tc_ld(src + (long long)r * sr + (long long)(k + i) * sc);
-        tc_split((float)v, h[i], l[i]);
-      }
-      const size_t off = canon_index(R, r, k);
+      for (int i = 0; i < 4; i++) tc_split((float)v[u][i], h[i], l[i]);
+      const size_t off = canon_index(R, rr[u], kk[u]);
       *reinterpret_cast<float4*>(hi + off) = make_float4(h[0], h[1], h[2], h[3]);
       *reinterpret_cast<float4*>(lo + off) = make_float4(l[0], l[1], l[2], l[3]);
     }
