@@ -16,6 +16,7 @@ single-matrix factorization does not shard.  Prints one JSON line on rank 0.
 from __future__ import annotations
 
 import argparse
+import collections
 import json
 import os
 import statistics
@@ -104,6 +105,10 @@ def parse():
     ap.add_argument("--no-compare-fp64", action="store_true",
                     help="skip the FP64 factorization timed beside the mixed one (N = 1)")
     ap.add_argument("--scratch-b2", type=int, default=0, help="per-CTA scratch in units of b*b doubles")
+    ap.add_argument("--workload", default="yukawa", choices=["yukawa", "batched"],
+                    help="batched: 64 uneven Laplace 3D matrices in one graph-captured launch")
+    ap.add_argument("--batch", type=int, default=64)
+    ap.add_argument("--autotune-cache", default=None)
     return ap.parse_args()
 
 
@@ -314,6 +319,84 @@ def workload_name(args):
             f"seeds {s['seed_x']}/{s['seed_y']}")
 
 
+def run_batched(args, rank, world):
+    """The batched uneven workload: args.batch Laplace 3D matrices (m from
+    {4096, ..., 16384}, n = m/2, tol 1e-6, mixed precision) with tile sizes
+    and dense threshold chosen by the autotuner, factored by ONE persistent
+    launch replayed from a CUDA graph; the sum of separate blr_qr launches
+    of the same matrices is timed beside it."""
+    import torch
+    import torch.distributed as dist
+    from paper_2208_06194_gb300 import autotune, blr
+    from paper_2208_06194_gb300 import workloads as W
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        dist.init_process_group("nccl")
+    tol, prec = 1e-6, blr.BLR_PREC_MIXED
+    probs = W.batched_laplace3d(args.batch, 401 + 1000 * rank)
+    tuned = autotune.tune(probs, "laplace3d", tol, prec, cache_path=args.autotune_cache)
+    mats = []
+    for (m, n, sx, sy), bb in zip(probs, tuned["b"]):
+        pr = W.kernel_problem("laplace3d", m, n, bb, sx, sy)
+        o = blr.blr_opts_default(b=bb, tol=tol, precision=prec, dense_rank=tuned["dense_rank"])
+        mats.append(blr.blr_compress_kernel(pr.x, pr.y, "laplace3d", o))
+    opts = blr.blr_opts_default(b=512, tol=tol, precision=prec, dense_rank=tuned["dense_rank"])
+    plan = blr.BatchPlan(mats, opts)
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            plan.launch(stream=stream.cuda_stream)
+            plan.finish(stream=stream.cuda_stream)
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph, stream=stream):
+            plan.launch(stream=stream.cuda_stream)
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        clocks = ClockSampler(local)
+        clocks.start()
+        times = []
+        for _ in range(args.steps):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            graph.replay()
+            e1.record(stream)
+            e1.synchronize()
+            plan.finish(stream=stream.cuda_stream)
+            times.append(e0.elapsed_time(e1) * 1e-3)
+        clk = clocks.stop()
+    t_batch = max_over_ranks(statistics.median(times), world, dist, dev)
+    st = blr.blr_stats(plan.factor(0))
+    # the same matrices one launch each (device time of each blr_qr)
+    t_sep = 0.0
+    for mm in mats:
+        f = blr.blr_qr(blr.blr_matrix_clone(mm), opts)
+        t_sep += blr.blr_stats(f)["seconds"]
+        f.destroy()
+    del graph
+    plan.destroy()
+    if rank == 0:
+        line = {"metric": f"BLR-QR of a batch of {args.batch} uneven Laplace 3D matrices, one persistent launch",
+                "value": job_value(t_batch, world), "unit": "s", "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": t_batch * 1e3, "higher_is_better": False, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f64 panels + 3xtf32/f32 updates", "data": "synthetic",
+                "config": {"workload": f"{args.batch} x laplace3d, m in 4096..16384, n = m/2, tol {tol:g}",
+                           "global_batch": args.batch * world, "tile_sizes": dict(collections.Counter(tuned["b"])),
+                           "dense_rank": tuned["dense_rank"], "launch": "CUDA graph replay of blr_batch_plan_launch",
+                           "l2": "inputs larger than L2"},
+                "separate_launches_seconds": t_sep, "batch_speedup": t_sep / t_batch,
+                "tasks": st["tasks"], "flops_counted": st["flops"][4], "autotune": tuned["table"],
+                "clocks": clk, "gpu_launches": args.steps}
+        print(json.dumps(line), flush=True)
+    for mm in mats:
+        mm.destroy()
+    if world > 1:
+        dist.destroy_process_group()
+
+
 def main():
     args = parse()
     if args.dense_rank == 0:
@@ -323,6 +406,9 @@ def main():
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         run_reference(args, rank, world)
+        return
+    if args.workload == "batched":
+        run_batched(args, rank, world)
         return
     import torch
     import torch.distributed as dist

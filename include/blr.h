@@ -45,6 +45,7 @@ extern "C" {
 
 typedef struct blr_matrix blr_matrix; /* opaque BLR matrix (device tiles + ranks) */
 typedef struct blr_factor blr_factor; /* opaque factor: in-place R/Y~ tiles + T panels */
+typedef struct blr_batch_plan blr_batch_plan; /* opaque launch plan for one or several matrices */
 
 /*
  * Options.  Zero-initialise, then set what you need (blr_opts_default fills
@@ -93,7 +94,8 @@ typedef struct blr_stats_t {
                                (GEQRT, LARFB, TSQRT, TPMQRT, total) */
   long long tasks[4];       /* factor only: tasks executed per type */
   double task_seconds[4];   /* factor only: summed task durations per type (CTA-seconds) */
-  double seconds;           /* factor only: device time of the factorization kernel */
+  double seconds;           /* factor only: device time of the factorization kernel (0 when
+                               the launch ran inside a CUDA graph) */
   long long tpmqrt_kind[8]; /* factor only: trapezoidal updates by operand kinds, index
                                4 (Y~_ik dense) + 2 (R_kj dense) + (A_ij dense) at task start */
   double tpmqrt_kind_seconds[8]; /* factor only: their summed durations (CTA-seconds) */
@@ -182,6 +184,47 @@ int blr_matrix_clone(const blr_matrix* a, blr_matrix** out, void* stream);
  * the factor is not created and the consumed matrix is freed.
  */
 int blr_qr(blr_matrix* a, const blr_opts* opts, blr_factor** f, void* stream);
+
+/*
+ * blr_qr_batched -- blr_qr of count independent matrices (each with its own
+ * m, n, b, ranks) in ONE persistent scheduler launch: the tile DAGs of all
+ * matrices share the ready queues, so small matrices fill the SMs together.
+ * Every a[i] is consumed exactly as by blr_qr (also on error) and f[i]
+ * receives its factor.  opts applies to all (precision, tolerances, dense
+ * threshold (capped at each matrix's b/2), scheduler width, watchdog); the
+ * statistics of every factor describe the whole launch.  Results are the
+ * same as count separate blr_qr calls (each tile's writer order is fixed by
+ * its own DAG).  Errors as blr_qr.
+ */
+int blr_qr_batched(blr_matrix** a, int count, const blr_opts* opts, blr_factor** f, void* stream);
+
+/*
+ * Launch plans: the same factorization(s) split so that the launch itself can
+ * be captured in a CUDA graph and replayed.
+ *  blr_batch_plan_create  allocates everything one launch over the matrices
+ *                         a[0..count) needs (factor storage, T blocks,
+ *                         scheduler state, scratch) and uploads the static
+ *                         scheduler state.  The matrices are NOT consumed: each
+ *                         launch restores the factor storage from them, so
+ *                         they must stay alive and unchanged while the plan
+ *                         is used.
+ *  blr_batch_plan_launch  device-side copies and memsets, then the persistent
+ *                         kernel, ordered on the stream: no allocation and no
+ *                         host synchronisation (capturable; replaying the
+ *                         graph re-factors the same inputs).
+ *  blr_batch_plan_finish  waits for the stream and reads the device status
+ *                         (BLR_ERR_TIMEOUT, BLR_ERR_NUMERIC, ... as blr_qr).
+ *  blr_batch_plan_factor  the plan-owned factor i (valid until destroy; its
+ *                         content is the last finished launch's), usable
+ *                         with every function taking a const blr_factor*.
+ * Calls on one plan must not overlap on the GPU.
+ */
+int blr_batch_plan_create(blr_matrix* const* a, int count, const blr_opts* opts, blr_batch_plan** plan,
+                          void* stream);
+int blr_batch_plan_launch(blr_batch_plan* plan, void* stream);
+int blr_batch_plan_finish(blr_batch_plan* plan, void* stream);
+const blr_factor* blr_batch_plan_factor(const blr_batch_plan* plan, int i);
+void blr_batch_plan_destroy(blr_batch_plan* plan);
 
 /*
  * blr_apply_qt -- in place on a device matrix B (m x nrhs, ldb >= m):

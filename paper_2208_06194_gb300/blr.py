@@ -64,6 +64,12 @@ _SIGS = {
     "blr_matrix_export": (_I, [_P, _I, _IP, _DP, _P]),
     "blr_matrix_clone": (_I, [_P, ctypes.POINTER(_P), _P]),
     "blr_qr": (_I, [_P, ctypes.POINTER(Opts), ctypes.POINTER(_P), _P]),
+    "blr_qr_batched": (_I, [ctypes.POINTER(_P), _I, ctypes.POINTER(Opts), ctypes.POINTER(_P), _P]),
+    "blr_batch_plan_create": (_I, [ctypes.POINTER(_P), _I, ctypes.POINTER(Opts), ctypes.POINTER(_P), _P]),
+    "blr_batch_plan_launch": (_I, [_P, _P]),
+    "blr_batch_plan_finish": (_I, [_P, _P]),
+    "blr_batch_plan_factor": (_P, [_P, _I]),
+    "blr_batch_plan_destroy": (None, [_P]),
     "blr_apply_qt": (_I, [_P, _P, _I, _I, _I, _P]),
     "blr_apply_qt_noalloc": (_I, [_P, _P, _I, _I, _I, _P]),
     "blr_lstsq": (_I, [_P, _P, _P, _I, _P, _I, _I, _I, _P]),
@@ -258,6 +264,55 @@ def blr_qr(a: Matrix, opts: Opts, stream=None) -> Factor:
     handle, a.handle = a.handle, None
     _check(lib().blr_qr(handle, ctypes.byref(opts), ctypes.byref(h), _stream(stream)))
     return Factor(h, a.m, a.n, a.b)
+
+
+def blr_qr_batched(mats: list, opts: Opts, stream=None) -> list:
+    """One persistent launch for all matrices; consumes them (like blr_qr)."""
+    n = len(mats)
+    arr = (_P * n)(*[m.handle for m in mats])
+    out = (_P * n)()
+    for m in mats:
+        m.handle = None
+    _check(lib().blr_qr_batched(arr, n, ctypes.byref(opts), out, _stream(stream)))
+    return [Factor(ctypes.c_void_p(out[i]), mats[i].m, mats[i].n, mats[i].b) for i in range(n)]
+
+
+class BatchPlan:
+    """A launch plan (blr_batch_plan_*): launch() is capturable in a CUDA
+    graph; the matrices must outlive the plan and stay unchanged."""
+
+    def __init__(self, mats: list, opts: Opts, stream=None):
+        n = len(mats)
+        arr = (_P * n)(*[m.handle for m in mats])
+        h = ctypes.c_void_p()
+        _check(lib().blr_batch_plan_create(arr, n, ctypes.byref(opts), ctypes.byref(h), _stream(stream)))
+        self.handle, self.mats = h, list(mats)
+
+    def launch(self, stream=None):
+        _check(lib().blr_batch_plan_launch(self.handle, _stream(stream)))
+
+    def finish(self, stream=None):
+        _check(lib().blr_batch_plan_finish(self.handle, _stream(stream)))
+
+    def factor(self, i: int) -> "Factor":
+        """A non-owning view of the plan's factor i."""
+        h = lib().blr_batch_plan_factor(self.handle, i)
+        m = self.mats[i]
+        f = Factor(ctypes.c_void_p(h), m.m, m.n, m.b)
+        f.destroy = lambda: None          # owned by the plan
+        f.__del__ = lambda: None
+        return f
+
+    def destroy(self):
+        if self.handle:
+            lib().blr_batch_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
 
 
 def blr_apply_qt(f: Factor, bmat, trans: int = 0, stream=None) -> None:

@@ -226,23 +226,21 @@ extern "C" int blr_matrix_clone(const blr_matrix* a, blr_matrix** out, void* str
   return BLR_OK;
 }
 
-extern "C" int blr_qr(blr_matrix* a, const blr_opts* opts, blr_factor** f, void* stream) {
-  int rc;
-  if (!a || !f) { blr_set_error("NULL argument"); return BLR_ERR_INVALID; }
-  *f = nullptr;
-  if (!opts) { blr_set_error("opts is NULL"); free_matrix_storage(a); delete a; return BLR_ERR_INVALID; }
+static int check_qr_opts(const blr_opts* opts) {
+  if (!opts) { blr_set_error("opts is NULL"); return BLR_ERR_INVALID; }
   if (opts->rec_tol < 0 || (opts->rec_tol == 0 && opts->tol <= 0)) {
     blr_set_error("blr_qr needs rec_tol > 0 or tol > 0");
-    free_matrix_storage(a);
-    delete a;
     return BLR_ERR_INVALID;
   }
   if (opts->precision != BLR_PREC_FP64 && opts->precision != BLR_PREC_MIXED) {
     blr_set_error("unknown precision %d", opts->precision);
-    free_matrix_storage(a);
-    delete a;
     return BLR_ERR_INVALID;
   }
+  return BLR_OK;
+}
+
+// A factor that takes over a's storage (a is deleted) and owns new T blocks.
+static int factor_adopt(blr_matrix* a, const blr_opts* opts, blr_factor** out) {
   blr_factor* F = new blr_factor;
   memset(F, 0, sizeof(*F));
   F->a = *a;
@@ -251,16 +249,60 @@ extern "C" int blr_qr(blr_matrix* a, const blr_opts* opts, blr_factor** f, void*
   const int p = F->a.p, q = F->a.q, b = F->a.b;
   F->nt = 0;
   for (int k = 0; k < q; k++) F->nt += p - k;
-  rc = blr_cuda_check(cudaMalloc(&F->t, sizeof(double) * (size_t)F->nt * BLR_NB * b), "alloc T blocks");
-  if (!rc) rc = blr_launch_factor(F, opts, (cudaStream_t)stream);
+  int rc = blr_cuda_check(cudaMalloc(&F->t, sizeof(double) * (size_t)F->nt * BLR_NB * b), "alloc T blocks");
   if (rc) {
-    if (F->t) cudaFree(F->t);
     free_matrix_storage(&F->a);
     delete F;
     return rc;
   }
   F->a.bytes += sizeof(double) * (size_t)F->nt * BLR_NB * b;
+  *out = F;
+  return BLR_OK;
+}
+
+int blr_factor_alloc_like(const blr_matrix* a, const blr_opts* opts, blr_factor** out) {
+  blr_matrix* w = new blr_matrix;
+  int rc = alloc_matrix(w, a->m, a->n, a->b);
+  if (rc) { delete w; return rc; }
+  return factor_adopt(w, opts, out);
+}
+
+extern "C" int blr_qr(blr_matrix* a, const blr_opts* opts, blr_factor** f, void* stream) {
+  int rc;
+  if (!a || !f) { blr_set_error("NULL argument"); return BLR_ERR_INVALID; }
+  *f = nullptr;
+  if ((rc = check_qr_opts(opts))) { free_matrix_storage(a); delete a; return rc; }
+  blr_factor* F = nullptr;
+  if ((rc = factor_adopt(a, opts, &F))) return rc;
+  rc = blr_launch_factor(F, opts, (cudaStream_t)stream);
+  if (rc) {
+    blr_destroy_factor(F);
+    return rc;
+  }
   *f = F;
+  return BLR_OK;
+}
+
+extern "C" int blr_qr_batched(blr_matrix** a, int count, const blr_opts* opts, blr_factor** f, void* stream) {
+  if (!a || !f || count < 1) { blr_set_error("NULL argument or count < 1"); return BLR_ERR_INVALID; }
+  int rc = check_qr_opts(opts);
+  for (int m = 0; m < count && !rc; m++)
+    if (!a[m]) { blr_set_error("matrix %d is NULL", m); rc = BLR_ERR_INVALID; }
+  std::vector<blr_factor*> fs;
+  for (int m = 0; m < count; m++) {
+    f[m] = nullptr;
+    if (!a[m]) continue;
+    if (rc) { free_matrix_storage(a[m]); delete a[m]; continue; }
+    blr_factor* F = nullptr;
+    rc = factor_adopt(a[m], opts, &F);
+    if (!rc) fs.push_back(F);
+  }
+  if (!rc) rc = blr_launch_factors(fs.data(), count, opts, (cudaStream_t)stream);
+  if (rc) {
+    for (blr_factor* F : fs) blr_destroy_factor(F);
+    return rc;
+  }
+  for (int m = 0; m < count; m++) f[m] = fs[m];
   return BLR_OK;
 }
 

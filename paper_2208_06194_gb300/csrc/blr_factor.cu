@@ -9,78 +9,134 @@
 #include "blr_dag.h"
 
 // ---------------------------------------------------------------------------
-// Host side of blr_qr
+// Host side: a launch plan for one persistent scheduler launch over the tile
+// DAGs of one or several matrices (a batch).  The plan holds every device
+// buffer the launch needs; plan_launch only resets state with device-side
+// copies and memsets and launches the kernel (no allocation, no host
+// synchronisation), so it can be captured in a CUDA graph; plan_finish reads
+// the status back.
 // ---------------------------------------------------------------------------
-int blr_launch_factor(blr_factor* f, const blr_opts* o, cudaStream_t st) {
-  blr_matrix& A = f->a;
-  const int p = A.p, q = A.q, b = A.b;
-  std::vector<int> offL(q + 1), offS(q + 1), offP(q + 1);
-  const int n_tasks = dag_offsets(p, q, offL.data(), offS.data(), offP.data());
-  DagShape d{p, q, offL.data(), offS.data(), offP.data()};
-  std::vector<int> deps(n_tasks);
-  for (int id = 0; id < n_tasks; id++) {
-    int i, j, k;
-    int t = dag_decode(d, id, &i, &j, &k);
-    deps[id] = dag_indegree(t, i, j, k);
-  }
-  std::vector<long long> toff(q);
-  long long acc = 0;
-  for (int k = 0; k < q; k++) { toff[k] = acc; acc += p - k; }
-
-  const int nsm = blr_num_sms();
-  int ctas = o->sched_ctas > 0 ? o->sched_ctas : nsm;
-  const size_t slab = (size_t)(o->scratch_b2 > 0 ? o->scratch_b2 : BLR_SLAB_B2) * b * b;
-
-  // one device block for all scheduler state
-  size_t bytes = 0;
-  auto take = [&](size_t n) { size_t off = bytes; bytes += (n + 255) & ~(size_t)255; return off; };
-  const size_t o_offL = take(sizeof(int) * (q + 1)), o_offS = take(sizeof(int) * (q + 1)),
-               o_offP = take(sizeof(int) * (q + 1)), o_toff = take(sizeof(long long) * q),
-               o_deps = take(sizeof(int) * n_tasks), o_qbuf = take(sizeof(int) * (size_t)BLR_NQ * n_tasks),
-               o_qh = take(sizeof(int) * 32 * BLR_NQ), o_qt = take(sizeof(int) * 32 * BLR_NQ),
-               o_done = take(sizeof(int)), o_status = take(sizeof(int)),
-               o_prog = take(sizeof(unsigned long long)), o_flops = take(sizeof(double) * 4),
-               o_ntask = take(sizeof(unsigned long long) * 4), o_tns = take(sizeof(unsigned long long) * 4),
-               o_nvar = take(sizeof(unsigned long long) * 8), o_tvar = take(sizeof(unsigned long long) * 8),
-               o_fvar = take(sizeof(double) * 8), o_peak = take(sizeof(unsigned long long));
-  char* base = nullptr;
+struct blr_batch_plan {
+  int count = 0;
+  blr_opts opts{};
+  std::vector<blr_factor*> fac;           // the factors (storage the launch writes)
+  std::vector<const blr_matrix*> src;     // graph mode: tiles restored from these at each launch
+  bool owns_factors = false;
+  char* base = nullptr;                   // device: static part, then the state reset per launch
+  size_t dyn_off = 0, dyn_bytes = 0;
+  int* deps0 = nullptr;                   // device: initial dependency counters
+  int* seed = nullptr;                    // device: the count initially ready tasks, then count
   double* scratch = nullptr;
-  if (cudaMalloc(&base, bytes) != cudaSuccess) { blr_set_error("blr_qr: out of device memory (scheduler state)"); return BLR_ERR_OOM; }
-  if (cudaMalloc(&scratch, sizeof(double) * slab * ctas) != cudaSuccess) {
-    cudaFree(base);
-    blr_set_error("blr_qr: out of device memory (scratch %zu MB)", sizeof(double) * slab * ctas >> 20);
-    return BLR_ERR_OOM;
-  }
-  // mixed path: tensor-core operands of every dense reflector block, one
-  // slot per (i,k) with i >= k (the T layout), 6 x Rp x b floats each; if the
-  // device cannot hold them the updates stage their operands themselves
   float* prep = nullptr;
-  const int prep_rp = (b + 127) / 128 * 128;
-  if (o->precision == BLR_PREC_MIXED) {
-    const size_t pbytes = (size_t)f->nt * 6 * prep_rp * b * sizeof(float);
-    if (cudaMalloc(&prep, pbytes) != cudaSuccess) {
-      prep = nullptr;
-      cudaGetLastError();
+  SchedParams P{};
+  int ctas = 0, n_tasks = 0;
+  size_t slab = 0;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+};
+
+static void plan_free(blr_batch_plan* pl) {
+  if (!pl) return;
+  if (pl->e0) cudaEventDestroy(pl->e0);
+  if (pl->e1) cudaEventDestroy(pl->e1);
+  if (pl->scratch) cudaFree(pl->scratch);
+  if (pl->prep) cudaFree(pl->prep);
+  if (pl->base) cudaFree(pl->base);
+#ifdef BLR_PHASE_TIMING
+  if (pl->P.phase) cudaFree(pl->P.phase);
+#endif
+  if (pl->owns_factors)
+    for (blr_factor* f : pl->fac) blr_destroy_factor(f);
+  delete pl;
+}
+
+// Builds the plan for factors whose storage (tiles, ranks, T) exists.
+static int plan_build(blr_factor* const* fs, int count, const blr_opts* o, blr_batch_plan** out) {
+  blr_batch_plan* pl = new blr_batch_plan;
+  pl->count = count;
+  pl->opts = *o;
+  pl->fac.assign(fs, fs + count);
+  struct Mat {
+    int p, q, b, nt;
+    std::vector<int> offL, offS, offP;
+    std::vector<long long> toff;
+    size_t o_offL, o_offS, o_offP, o_toff, prep_off;
+    int base;
+  };
+  std::vector<Mat> M(count);
+  int total = 0, bmax = 0;
+  size_t prep_floats = 0;
+  for (int m = 0; m < count; m++) {
+    const blr_matrix& A = fs[m]->a;
+    Mat& x = M[m];
+    x.p = A.p; x.q = A.q; x.b = A.b; x.nt = fs[m]->nt;
+    x.offL.resize(x.q + 1); x.offS.resize(x.q + 1); x.offP.resize(x.q + 1);
+    x.base = total;
+    total += dag_offsets(x.p, x.q, x.offL.data(), x.offS.data(), x.offP.data());
+    x.toff.resize(x.q);
+    long long acc = 0;
+    for (int k = 0; k < x.q; k++) { x.toff[k] = acc; acc += x.p - k; }
+    bmax = std::max(bmax, x.b);
+    x.prep_off = prep_floats;
+    prep_floats += (size_t)x.nt * 6 * ((x.b + 127) / 128 * 128) * x.b;
+  }
+  pl->n_tasks = total;
+  std::vector<int> deps(total);
+  for (int m = 0; m < count; m++) {
+    Mat& x = M[m];
+    DagShape d{x.p, x.q, x.offL.data(), x.offS.data(), x.offP.data()};
+    const int nm = (m + 1 < count ? M[m + 1].base : total) - x.base;
+    for (int id = 0; id < nm; id++) {
+      int i, j, k;
+      const int t = dag_decode(d, id, &i, &j, &k);
+      deps[x.base + id] = dag_indegree(t, i, j, k);
     }
   }
-  int rc = BLR_OK;
-  SchedParams P{};
-#ifdef BLR_PHASE_TIMING
-  cudaMalloc(&P.phase, 16 * sizeof(unsigned long long));
-  cudaMemset(P.phase, 0, 16 * sizeof(unsigned long long));
-#endif
-  P.prep = prep;
-  P.prep_rp = prep_rp;
-  P.p = p; P.q = q; P.b = b; P.cap = A.cap;
-  P.dense_rank = (o->dense_rank > 0 && o->dense_rank <= A.cap) ? o->dense_rank : A.cap;
+  // device layout: [static: per-matrix offsets, params, bases, deps0, seed][state]
+  size_t bytes = 0;
+  auto take = [&](size_t n) { size_t off = bytes; bytes += (n + 255) & ~(size_t)255; return off; };
+  for (int m = 0; m < count; m++) {
+    M[m].o_offL = take(sizeof(int) * (M[m].q + 1));
+    M[m].o_offS = take(sizeof(int) * (M[m].q + 1));
+    M[m].o_offP = take(sizeof(int) * (M[m].q + 1));
+    M[m].o_toff = take(sizeof(long long) * M[m].q);
+  }
+  const size_t o_mats = take(sizeof(SchedParams) * count), o_mbase = take(sizeof(int) * (count + 1)),
+               o_deps0 = take(sizeof(int) * total), o_seed = take(sizeof(int) * (count + 1));
+  pl->dyn_off = bytes;
+  const size_t o_deps = take(sizeof(int) * total), o_qbuf = take(sizeof(int) * (size_t)BLR_NQ * total),
+               o_qh = take(sizeof(int) * 32 * BLR_NQ), o_qt = take(sizeof(int) * 32 * BLR_NQ),
+               o_done = take(sizeof(int)), o_status = take(sizeof(int)), o_prog = take(sizeof(unsigned long long)),
+               o_flops = take(sizeof(double) * 4), o_ntask = take(sizeof(unsigned long long) * 4),
+               o_tns = take(sizeof(unsigned long long) * 4), o_nvar = take(sizeof(unsigned long long) * 8),
+               o_tvar = take(sizeof(unsigned long long) * 8), o_fvar = take(sizeof(double) * 8),
+               o_peak = take(sizeof(unsigned long long));
+  pl->dyn_bytes = bytes - pl->dyn_off;
+  const int nsm = blr_num_sms();
+  pl->ctas = o->sched_ctas > 0 ? o->sched_ctas : nsm;
+  pl->slab = (size_t)(o->scratch_b2 > 0 ? o->scratch_b2 : BLR_SLAB_B2) * bmax * bmax;
+  if (cudaMalloc(&pl->base, bytes) != cudaSuccess) {
+    plan_free(pl);
+    blr_set_error("blr_qr: out of device memory (scheduler state)");
+    return BLR_ERR_OOM;
+  }
+  if (cudaMalloc(&pl->scratch, sizeof(double) * pl->slab * pl->ctas) != cudaSuccess) {
+    const size_t mb = sizeof(double) * pl->slab * pl->ctas >> 20;
+    plan_free(pl);
+    blr_set_error("blr_qr: out of device memory (scratch %zu MB)", mb);
+    return BLR_ERR_OOM;
+  }
+  // mixed path: tensor-core operands of every dense reflector block (one slot
+  // per (i,k), i >= k); if the device cannot hold them the updates stage
+  // their operands themselves
+  if (o->precision == BLR_PREC_MIXED && cudaMalloc(&pl->prep, sizeof(float) * prep_floats) != cudaSuccess) {
+    pl->prep = nullptr;
+    cudaGetLastError();
+  }
+  char* base = pl->base;
+  SchedParams& P = pl->P;
   P.precision = o->precision;
   P.rec_tol = o->rec_tol > 0 ? o->rec_tol : o->tol;
-  P.tiles = A.tiles; P.rank = A.rank; P.t = f->t;
-  P.toff_dev = (const long long*)(base + o_toff);
-  P.off_larfb = (const int*)(base + o_offL);
-  P.off_tsqrt = (const int*)(base + o_offS);
-  P.off_tpmqrt = (const int*)(base + o_offP);
-  P.n_tasks = n_tasks;
+  P.n_tasks = total;
   P.deps = (int*)(base + o_deps);
   P.qbuf = (int*)(base + o_qbuf);
   P.qhead = (int*)(base + o_qh);
@@ -89,8 +145,8 @@ int blr_launch_factor(blr_factor* f, const blr_opts* o, cudaStream_t st) {
   P.status = (int*)(base + o_status);
   P.progress_ns = (unsigned long long*)(base + o_prog);
   P.watchdog_ns = (long long)(o->watchdog_ms > 0 ? o->watchdog_ms : 20000) * 1000000ll;
-  P.scratch = scratch;
-  P.slab = slab;
+  P.scratch = pl->scratch;
+  P.slab = pl->slab;
   P.flops = (double*)(base + o_flops);
   P.ntask = (unsigned long long*)(base + o_ntask);
   P.tns = (unsigned long long*)(base + o_tns);
@@ -98,47 +154,117 @@ int blr_launch_factor(blr_factor* f, const blr_opts* o, cudaStream_t st) {
   P.tvar = (unsigned long long*)(base + o_tvar);
   P.fvar = (double*)(base + o_fvar);
   P.slab_peak = (unsigned long long*)(base + o_peak);
+#ifdef BLR_PHASE_TIMING
+  cudaMalloc(&P.phase, 16 * sizeof(unsigned long long));
+  cudaMemset(P.phase, 0, 16 * sizeof(unsigned long long));
+#endif
+  std::vector<SchedParams> mats(count, P);
+  std::vector<int> mbase(count + 1), seed(count + 1);
+  int rc = BLR_OK;
+  for (int m = 0; m < count && !rc; m++) {
+    const blr_matrix& A = fs[m]->a;
+    SchedParams& Q = mats[m];
+    Q.p = A.p; Q.q = A.q; Q.b = A.b; Q.cap = A.cap;
+    Q.dense_rank = (o->dense_rank > 0 && o->dense_rank <= A.cap) ? o->dense_rank : A.cap;
+    Q.tiles = A.tiles; Q.rank = A.rank; Q.t = fs[m]->t;
+    Q.toff_dev = (const long long*)(base + M[m].o_toff);
+    Q.off_larfb = (const int*)(base + M[m].o_offL);
+    Q.off_tsqrt = (const int*)(base + M[m].o_offS);
+    Q.off_tpmqrt = (const int*)(base + M[m].o_offP);
+    Q.prep = pl->prep ? pl->prep + M[m].prep_off : nullptr;
+    Q.prep_rp = (A.b + 127) / 128 * 128;
+    Q.task_base = M[m].base;
+    mbase[m] = M[m].base;
+    seed[m] = M[m].base;   // GEQRT(0) of every matrix is ready at the start
+    rc = blr_cuda_check(cudaMemcpy(base + M[m].o_offL, M[m].offL.data(), sizeof(int) * (M[m].q + 1), cudaMemcpyHostToDevice), "copy offsets");
+    if (!rc) rc = blr_cuda_check(cudaMemcpy(base + M[m].o_offS, M[m].offS.data(), sizeof(int) * (M[m].q + 1), cudaMemcpyHostToDevice), "copy offsets");
+    if (!rc) rc = blr_cuda_check(cudaMemcpy(base + M[m].o_offP, M[m].offP.data(), sizeof(int) * (M[m].q + 1), cudaMemcpyHostToDevice), "copy offsets");
+    if (!rc) rc = blr_cuda_check(cudaMemcpy(base + M[m].o_toff, M[m].toff.data(), sizeof(long long) * M[m].q, cudaMemcpyHostToDevice), "copy T offsets");
+  }
+  mbase[count] = total;
+  seed[count] = count;
+  for (int m = 0; m < count; m++) {
+    mats[m].nmat = count;
+    mats[m].mats = (const SchedParams*)(base + o_mats);
+    mats[m].mat_base = (const int*)(base + o_mbase);
+  }
+  if (count == 1) {
+    P = mats[0];
+    P.nmat = 1;
+  } else {
+    // batch-level parameters: matrix 0's shape (unused: every task looks up its own)
+    SchedParams shared = mats[0];
+    P = shared;
+  }
+  if (!rc) rc = blr_cuda_check(cudaMemcpy(base + o_mats, mats.data(), sizeof(SchedParams) * count, cudaMemcpyHostToDevice), "copy params");
+  if (!rc) rc = blr_cuda_check(cudaMemcpy(base + o_mbase, mbase.data(), sizeof(int) * (count + 1), cudaMemcpyHostToDevice), "copy bases");
+  if (!rc) rc = blr_cuda_check(cudaMemcpy(base + o_deps0, deps.data(), sizeof(int) * total, cudaMemcpyHostToDevice), "copy deps");
+  if (!rc) rc = blr_cuda_check(cudaMemcpy(base + o_seed, seed.data(), sizeof(int) * (count + 1), cudaMemcpyHostToDevice), "copy seed");
+  pl->deps0 = (int*)(base + o_deps0);
+  pl->seed = (int*)(base + o_seed);
+  if (!rc) rc = blr_cuda_check(cudaEventCreate(&pl->e0), "event");
+  if (!rc) rc = blr_cuda_check(cudaEventCreate(&pl->e1), "event");
+  if (rc) {
+    plan_free(pl);
+    return rc;
+  }
+  *out = pl;
+  return BLR_OK;
+}
 
-  cudaEvent_t e0 = nullptr, e1 = nullptr;
-  do {
-    if ((rc = blr_cuda_check(cudaMemsetAsync(base, 0, bytes, st), "memset scheduler"))) break;
-    if ((rc = blr_cuda_check(cudaMemsetAsync(P.qbuf, 0xff, sizeof(int) * (size_t)BLR_NQ * n_tasks, st), "memset queues"))) break;
-    if ((rc = blr_cuda_check(cudaMemcpyAsync((void*)P.off_larfb, offL.data(), sizeof(int) * (q + 1), cudaMemcpyHostToDevice, st), "copy offsets"))) break;
-    if ((rc = blr_cuda_check(cudaMemcpyAsync((void*)P.off_tsqrt, offS.data(), sizeof(int) * (q + 1), cudaMemcpyHostToDevice, st), "copy offsets"))) break;
-    if ((rc = blr_cuda_check(cudaMemcpyAsync((void*)P.off_tpmqrt, offP.data(), sizeof(int) * (q + 1), cudaMemcpyHostToDevice, st), "copy offsets"))) break;
-    if ((rc = blr_cuda_check(cudaMemcpyAsync((void*)P.toff_dev, toff.data(), sizeof(long long) * q, cudaMemcpyHostToDevice, st), "copy T offsets"))) break;
-    if ((rc = blr_cuda_check(cudaMemcpyAsync(P.deps, deps.data(), sizeof(int) * n_tasks, cudaMemcpyHostToDevice, st), "copy deps"))) break;
-    // the only initially ready task: GEQRT(0) in queue 0
-    int first = 0, one = 1;
-    if ((rc = blr_cuda_check(cudaMemcpyAsync(P.qbuf, &first, sizeof(int), cudaMemcpyHostToDevice, st), "seed queue"))) break;
-    if ((rc = blr_cuda_check(cudaMemcpyAsync(P.qtail, &one, sizeof(int), cudaMemcpyHostToDevice, st), "seed queue"))) break;
-    cudaEventCreate(&e0);
-    cudaEventCreate(&e1);
-    cudaEventRecord(e0, st);
-    rc = (P.precision == BLR_PREC_MIXED) ? blr_run_factor_mixed(P, ctas, st) : blr_run_factor_fp64(P, ctas, st);
-    if (rc) break;
-    cudaEventRecord(e1, st);
-    if ((rc = blr_cuda_check(cudaStreamSynchronize(st), "k_factor"))) break;
-    float ms = 0.f;
-    cudaEventElapsedTime(&ms, e0, e1);
+// Capturable: device-side resets and the kernel launch only.
+static int plan_launch(blr_batch_plan* pl, cudaStream_t st) {
+  int rc = BLR_OK;
+  for (size_t m = 0; m < pl->src.size() && !rc; m++) {
+    const blr_matrix& S = *pl->src[m];
+    blr_matrix& A = pl->fac[m]->a;
+    rc = blr_cuda_check(cudaMemcpyAsync(A.tiles, S.tiles, sizeof(double) * (size_t)A.p * A.q * A.b * A.b,
+                                        cudaMemcpyDeviceToDevice, st), "restore tiles");
+    if (!rc) rc = blr_cuda_check(cudaMemcpyAsync(A.rank, S.rank, sizeof(int) * A.p * A.q, cudaMemcpyDeviceToDevice, st),
+                                 "restore ranks");
+  }
+  SchedParams& P = pl->P;
+  if (!rc) rc = blr_cuda_check(cudaMemsetAsync(pl->base + pl->dyn_off, 0, pl->dyn_bytes, st), "reset scheduler");
+  if (!rc) rc = blr_cuda_check(cudaMemcpyAsync(P.deps, pl->deps0, sizeof(int) * pl->n_tasks, cudaMemcpyDeviceToDevice, st), "reset deps");
+  if (!rc) rc = blr_cuda_check(cudaMemsetAsync(P.qbuf, 0xff, sizeof(int) * (size_t)BLR_NQ * pl->n_tasks, st), "reset queues");
+  if (!rc) rc = blr_cuda_check(cudaMemcpyAsync(P.qbuf, pl->seed, sizeof(int) * pl->count, cudaMemcpyDeviceToDevice, st), "seed queue");
+  if (!rc) rc = blr_cuda_check(cudaMemcpyAsync(P.qtail, pl->seed + pl->count, sizeof(int), cudaMemcpyDeviceToDevice, st), "seed queue");
+  if (!rc) rc = blr_cuda_check(cudaEventRecord(pl->e0, st), "event");
+  if (!rc) rc = (P.precision == BLR_PREC_MIXED) ? blr_run_factor_mixed(P, pl->ctas, st) : blr_run_factor_fp64(P, pl->ctas, st);
+  if (!rc) rc = blr_cuda_check(cudaEventRecord(pl->e1, st), "event");
+  return rc;
+}
+
+// Waits for the launch, reads its status and statistics into every factor.
+static int plan_finish(blr_batch_plan* pl, cudaStream_t st) {
+  int rc = blr_cuda_check(cudaStreamSynchronize(st), "k_factor");
+  if (rc) return rc;
+  SchedParams& P = pl->P;
+  float ms = 0.f;
+  if (cudaEventElapsedTime(&ms, pl->e0, pl->e1) != cudaSuccess) {
+    ms = 0.f;                 // no device time (e.g. the launch ran as part of a CUDA graph)
+    cudaGetLastError();
+  }
+  int status = 0, done = 0;
+  double fl[4];
+  unsigned long long nt[4], tns[4], nv[8], tv[8], peak = 0;
+  double fv[8];
+  cudaMemcpy(&status, P.status, sizeof(int), cudaMemcpyDeviceToHost);
+  cudaMemcpy(&done, P.done, sizeof(int), cudaMemcpyDeviceToHost);
+  cudaMemcpy(fl, P.flops, sizeof(fl), cudaMemcpyDeviceToHost);
+  cudaMemcpy(nt, P.ntask, sizeof(nt), cudaMemcpyDeviceToHost);
+  cudaMemcpy(tns, P.tns, sizeof(tns), cudaMemcpyDeviceToHost);
+  cudaMemcpy(nv, P.nvar, sizeof(nv), cudaMemcpyDeviceToHost);
+  cudaMemcpy(tv, P.tvar, sizeof(tv), cudaMemcpyDeviceToHost);
+  cudaMemcpy(fv, P.fvar, sizeof(fv), cudaMemcpyDeviceToHost);
+  cudaMemcpy(&peak, P.slab_peak, sizeof(peak), cudaMemcpyDeviceToHost);
+  rc = blr_cuda_check(cudaGetLastError(), "read status");
+  if (rc) return rc;
+  // statistics of the whole launch (a batch reports the batch in every factor)
+  for (blr_factor* f : pl->fac) {
     f->seconds = ms * 1e-3;
-    int status = 0, done = 0;
-    double fl[4];
-    unsigned long long nt[4], tns[4];
-    cudaMemcpy(tns, P.tns, sizeof(tns), cudaMemcpyDeviceToHost);
-    cudaMemcpy(&status, P.status, sizeof(int), cudaMemcpyDeviceToHost);
-    cudaMemcpy(&done, P.done, sizeof(int), cudaMemcpyDeviceToHost);
-    cudaMemcpy(fl, P.flops, sizeof(fl), cudaMemcpyDeviceToHost);
-    cudaMemcpy(nt, P.ntask, sizeof(nt), cudaMemcpyDeviceToHost);
-    unsigned long long nv[8], tv[8];
-    double fv[8];
-    cudaMemcpy(nv, P.nvar, sizeof(nv), cudaMemcpyDeviceToHost);
-    cudaMemcpy(tv, P.tvar, sizeof(tv), cudaMemcpyDeviceToHost);
-    cudaMemcpy(fv, P.fvar, sizeof(fv), cudaMemcpyDeviceToHost);
-    unsigned long long peak = 0;
-    cudaMemcpy(&peak, P.slab_peak, sizeof(peak), cudaMemcpyDeviceToHost);
     f->scratch_peak_bytes = (long long)(peak * sizeof(double));
-    f->scratch_bytes = (long long)(sizeof(double) * slab * ctas);
+    f->scratch_bytes = (long long)(sizeof(double) * pl->slab * pl->ctas);
     for (int v = 0; v < 8; v++) {
       f->tpmqrt_kind[v] = (long long)nv[v];
       f->tpmqrt_kind_seconds[v] = tv[v] * 1e-9;
@@ -151,16 +277,7 @@ int blr_launch_factor(blr_factor* f, const blr_opts* o, cudaStream_t st) {
       f->tasks[t] = (long long)nt[t];
       f->task_seconds[t] = tns[t] * 1e-9;
     }
-    if (status & ST_TIMEOUT) { blr_set_error("blr_qr: scheduler watchdog expired (%d of %d tasks done)", done, n_tasks); rc = BLR_ERR_TIMEOUT; break; }
-    if (status & ST_NUMERIC) { blr_set_error("blr_qr: non-finite Householder coefficient"); rc = BLR_ERR_NUMERIC; break; }
-    if (status & ST_RANK) { blr_set_error("blr_qr: scratch slab exceeded"); rc = BLR_ERR_RANK_OVERFLOW; break; }
-    if (status != 0 || done != n_tasks) { blr_set_error("blr_qr: scheduler ended with status %d, %d of %d tasks", status, done, n_tasks); rc = BLR_ERR_CUDA; break; }
-  } while (0);
-  if (e0) cudaEventDestroy(e0);
-  if (e1) cudaEventDestroy(e1);
-  cudaFree(scratch);
-  cudaFree(base);
-  if (prep) cudaFree(prep);
+  }
 #ifdef BLR_PHASE_TIMING
   {
     unsigned long long ph[16];
@@ -168,11 +285,70 @@ int blr_launch_factor(blr_factor* f, const blr_opts* o, cudaStream_t st) {
     fprintf(stderr, "blr_qr phases (CTA-s):");
     for (int i2 = 0; i2 < 16; i2++) fprintf(stderr, " %d:%.2f", i2, ph[i2] * 1e-9);
     fprintf(stderr, "\n");
-    cudaFree(P.phase);
   }
 #endif
+  const int n_tasks = pl->n_tasks;
+  if (status & ST_TIMEOUT) { blr_set_error("blr_qr: scheduler watchdog expired (%d of %d tasks done)", done, n_tasks); return BLR_ERR_TIMEOUT; }
+  if (status & ST_NUMERIC) { blr_set_error("blr_qr: non-finite Householder coefficient"); return BLR_ERR_NUMERIC; }
+  if (status & ST_RANK) { blr_set_error("blr_qr: scratch slab exceeded"); return BLR_ERR_RANK_OVERFLOW; }
+  if (status != 0 || done != n_tasks) { blr_set_error("blr_qr: scheduler ended with status %d, %d of %d tasks", status, done, n_tasks); return BLR_ERR_CUDA; }
+  return BLR_OK;
+}
+
+int blr_launch_factors(blr_factor* const* fs, int count, const blr_opts* o, cudaStream_t st) {
+  blr_batch_plan* pl = nullptr;
+  int rc = plan_build(fs, count, o, &pl);
+  if (rc) return rc;
+  rc = plan_launch(pl, st);
+  if (!rc) rc = plan_finish(pl, st);
+  else cudaStreamSynchronize(st);
+  plan_free(pl);
   return rc;
 }
+
+int blr_launch_factor(blr_factor* f, const blr_opts* o, cudaStream_t st) { return blr_launch_factors(&f, 1, o, st); }
+
+// ---- C ABI of launch plans (graph capture) --------------------------------
+extern "C" int blr_batch_plan_create(blr_matrix* const* a, int count, const blr_opts* opts, blr_batch_plan** out,
+                                     void* stream) {
+  if (!a || !opts || !out || count < 1) { blr_set_error("NULL argument or count < 1"); return BLR_ERR_INVALID; }
+  *out = nullptr;
+  std::vector<blr_factor*> fs;
+  int rc = BLR_OK;
+  for (int m = 0; m < count && !rc; m++) {
+    blr_factor* f = nullptr;
+    rc = blr_factor_alloc_like(a[m], opts, &f);
+    if (!rc) fs.push_back(f);
+  }
+  blr_batch_plan* pl = nullptr;
+  if (!rc) rc = plan_build(fs.data(), count, opts, &pl);
+  if (rc) {
+    for (blr_factor* f : fs) blr_destroy_factor(f);
+    return rc;
+  }
+  pl->owns_factors = true;
+  pl->src.assign(a, a + count);
+  (void)stream;
+  *out = pl;
+  return BLR_OK;
+}
+
+extern "C" int blr_batch_plan_launch(blr_batch_plan* plan, void* stream) {
+  if (!plan) { blr_set_error("NULL plan"); return BLR_ERR_INVALID; }
+  return plan_launch(plan, (cudaStream_t)stream);
+}
+
+extern "C" int blr_batch_plan_finish(blr_batch_plan* plan, void* stream) {
+  if (!plan) { blr_set_error("NULL plan"); return BLR_ERR_INVALID; }
+  return plan_finish(plan, (cudaStream_t)stream);
+}
+
+extern "C" const blr_factor* blr_batch_plan_factor(const blr_batch_plan* plan, int i) {
+  if (!plan || i < 0 || i >= plan->count) return nullptr;
+  return plan->fac[i];
+}
+
+extern "C" void blr_batch_plan_destroy(blr_batch_plan* plan) { plan_free(plan); }
 
 // Host-side check of the DAG formulas (no device work): builds the DAG from
 // dag_successors, checks every in-degree against dag_indegree, and runs the

@@ -96,6 +96,14 @@ struct SchedParams {
   int prep_rp;                   // rows of those operands (b rounded up to 128)
   unsigned long long* phase;     // 16 phase-time counters (builds with BLR_PHASE_TIMING only)
   unsigned long long* slab_peak; // largest scratch use of any task (doubles)
+  // batches: several matrices in one launch.  Every matrix has its own copy
+  // of these parameters (shape, tiles, T, DAG offsets, prepared operands)
+  // sharing the scheduler state above; task ids are batch-wide, matrix t's
+  // first task is task_base.
+  int task_base;
+  int nmat;                      // > 1: a batch (mats, mat_base valid)
+  const SchedParams* mats;       // device, nmat entries
+  const int* mat_base;           // device, nmat + 1 entries (task_base of each, then the total)
 };
 
 // host helpers (blr_api.cu)
@@ -105,6 +113,8 @@ int blr_num_sms();
 
 // kernel launchers implemented in the .cu files
 int blr_launch_factor(blr_factor* f, const blr_opts* o, cudaStream_t st);
+int blr_launch_factors(blr_factor* const* fs, int count, const blr_opts* o, cudaStream_t st);
+int blr_factor_alloc_like(const blr_matrix* a, const blr_opts* opts, blr_factor** out);
 int blr_run_factor_fp64(const SchedParams& P, int ctas, cudaStream_t st);
 int blr_run_factor_mixed(const SchedParams& P, int ctas, cudaStream_t st);
 int blr_compress_impl(const double* a_dev, int lda, const double* x_dev, const double* y_dev,

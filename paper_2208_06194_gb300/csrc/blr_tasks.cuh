@@ -81,12 +81,15 @@ __device__ __forceinline__ int ld_rank(const int* p) { return __ldcg(p); }
 __device__ void q_push(const SchedParams& P, int qi, int task);
 
 // Thread 0: one dependency of task sid is satisfied; queue it when ready.
+// sid is the task's id within its matrix (P, d); dependency counters and
+// queues hold batch-wide ids, task_base + sid.
 __device__ void release_task(const SchedParams& P, const DagShape& d, int sid) {
-  if (atomicSub(P.deps + sid, 1) == 1) {
+  const int gid = P.task_base + sid;
+  if (atomicSub(P.deps + gid, 1) == 1) {
     __threadfence();
     int si, sj, sk;
     const int st = dag_decode(d, sid, &si, &sj, &sk);
-    q_push(P, dag_queue(st, si, sj, sk), sid);
+    q_push(P, dag_queue(st, si, sj, sk), gid);
   }
 }
 
@@ -1036,6 +1039,7 @@ __global__ void __launch_bounds__(BLR_NT, 1) k_factor(SchedParams P) {
   c.status = P.status;
   DagShape d{P.p, P.q, P.off_larfb, P.off_tsqrt, P.off_tpmqrt};
   TaskEnv env{&P, P.scratch + (size_t)blockIdx.x * P.slab, 0, false, nullptr, nullptr, &d, -1, 0};
+  const SchedParams* Pm = &P;       // the parameters of the current task's matrix
   constexpr bool kTensor = std::is_same<S, float>::value;
   static_assert(BLR_SMEM_BYTES >= TC_STAGE_BYTES && TC_STAGE_BYTES >= 3 * 128 * 128 * 4, "staging area");
   __shared__ uint64_t tc_bars[2];
@@ -1078,8 +1082,21 @@ __global__ void __launch_bounds__(BLR_NT, 1) k_factor(SchedParams P) {
     const int task = task_sh;
     __syncthreads();
     if (task < 0) break;
+    // a batch (several matrices in one launch): find the task's matrix
+    if (P.nmat > 1) {
+      int lo = 0, hi = P.nmat - 1;
+      while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (__ldg(P.mat_base + mid) <= task) lo = mid;
+        else hi = mid - 1;
+      }
+      Pm = P.mats + lo;
+      d = DagShape{Pm->p, Pm->q, Pm->off_larfb, Pm->off_tsqrt, Pm->off_tpmqrt};
+      env.P = Pm;
+    }
+    const int local = task - Pm->task_base;
     int i, j, k;
-    const int type = dag_decode(d, task, &i, &j, &k);
+    const int type = dag_decode(d, local, &i, &j, &k);
     const unsigned long long t_start = gtimer();
     c.fma = 0.0;
     env.used = 0;
@@ -1088,8 +1105,8 @@ __global__ void __launch_bounds__(BLR_NT, 1) k_factor(SchedParams P) {
     // operand kinds of an update, for the statistics: 4 (Y dense) + 2 (R dense) + (A dense)
     int variant = 0;
     if (type == TASK_TPMQRT && threadIdx.x == 0)
-      variant = (ld_rank(rank_ptr(P, i, k)) < 0) * 4 + (ld_rank(rank_ptr(P, k, j)) < 0) * 2 +
-                (ld_rank(rank_ptr(P, i, j)) < 0);
+      variant = (ld_rank(rank_ptr(*Pm, i, k)) < 0) * 4 + (ld_rank(rank_ptr(*Pm, k, j)) < 0) * 2 +
+                (ld_rank(rank_ptr(*Pm, i, j)) < 0);
     switch (type) {
       case TASK_GEQRT: task_geqrt<S>(env, k, c); break;
       case TASK_LARFB: task_larfb<S>(env, k, j, c); break;
@@ -1105,7 +1122,7 @@ __global__ void __launch_bounds__(BLR_NT, 1) k_factor(SchedParams P) {
     __syncthreads();
     if (threadIdx.x == 0 && type >= 0) {
       dag_for_each_successor(d, type, i, j, k, [&](int sid) {
-        if (sid != env.skip_succ) release_task(P, d, sid);
+        if (sid != env.skip_succ) release_task(*Pm, d, sid);
       });
       const unsigned long long dt = gtimer() - t_start;
       atomicAdd(P.flops + type, 2.0 * c.fma);

@@ -175,3 +175,14 @@ def random_blr_dense(m: int, n: int, b: int, k: int, seed: int) -> np.ndarray:
 def gaussian_rhs(m: int, nrhs: int, seed: int) -> np.ndarray:
     """Right-hand sides B (m x nrhs), N(0,1)."""
     return np.random.default_rng(seed).standard_normal((m, nrhs))
+
+
+def batched_laplace3d(count: int = 64, seed: int = 401) -> list:
+    """The batched uneven workload: `count` independent problems, m drawn
+    uniformly from {4096, 6144, ..., 16384} (seed), n = m / 2, Laplace
+    kernel on 3D uniform points with per-problem seeds 4000 + 2 s and
+    4001 + 2 s.  Returns (m, n, seed_x, seed_y) tuples; the points are drawn
+    (and RCB-ordered for the chosen tile size) by kernel_problem."""
+    sizes = np.arange(4096, 16384 + 1, 2048)
+    ms = np.random.default_rng(seed).choice(sizes, size=count)
+    return [(int(m), int(m) // 2, 4000 + 2 * s, 4001 + 2 * s) for s, m in enumerate(ms)]
