@@ -108,6 +108,8 @@ def parse():
     ap.add_argument("--workload", default="yukawa", choices=["yukawa", "batched"],
                     help="batched: 64 uneven Laplace 3D matrices in one graph-captured launch")
     ap.add_argument("--batch", type=int, default=64)
+    ap.add_argument("--ill-conditioned", action="store_true",
+                    help="columns scaled by a geometric sequence from 1 to 1e-10 (Res and Orth reported)")
     ap.add_argument("--autotune-cache", default=None)
     return ap.parse_args()
 
@@ -172,6 +174,8 @@ def kernel_matrix_times(pr, z, torch, dev):
     blocks (check only; not part of the timed path)."""
     x = torch.from_numpy(pr.x).to(dev)
     y = torch.from_numpy(pr.y).to(dev)
+    if pr.col_scale is not None:
+        z = z * torch.from_numpy(pr.col_scale).to(dev)[:, None]
     out = torch.empty((pr.m, z.shape[1]), dtype=torch.float64, device=dev)
     for r0 in range(0, pr.m, 2048):
         d = torch.cdist(x[:, r0:r0 + 2048].T, y.T)
@@ -316,7 +320,7 @@ def job_value(t_step: float, world: int) -> float:
 def workload_name(args):
     s = SIZES[args.size]
     return (f"yukawa3d {s['m']}x{s['n']} b={s['b']} tol={args.tol:g} RCB-ordered points "
-            f"seeds {s['seed_x']}/{s['seed_y']}")
+            f"seeds {s['seed_x']}/{s['seed_y']}" + (", columns scaled 1..1e-10" if args.ill_conditioned else ""))
 
 
 def run_batched(args, rank, world):
@@ -419,11 +423,11 @@ def main():
     from paper_2208_06194_gb300 import blr
     from paper_2208_06194_gb300 import workloads as W
     s = SIZES[args.size]
-    pr = W.yukawa3d(s["m"], s["n"], s["b"], *replica_seeds(s, rank))
+    pr = W.yukawa3d(s["m"], s["n"], s["b"], *replica_seeds(s, rank), ill_conditioned=args.ill_conditioned)
     prec = blr.BLR_PREC_MIXED if args.precision == "mixed" else blr.BLR_PREC_FP64
     opts = blr.blr_opts_default(b=s["b"], tol=args.tol, precision=prec, dense_rank=args.dense_rank,
                                 scratch_b2=args.scratch_b2)
-    a0 = blr.blr_compress_kernel(pr.x, pr.y, "yukawa3d", opts)
+    a0 = blr.blr_compress_kernel(pr.x, pr.y, "yukawa3d", opts, col_scale=pr.col_scale)
     st_a = blr.blr_stats(a0)
     stream = torch.cuda.current_stream()
 
@@ -468,7 +472,7 @@ def main():
     if not args.no_compare_fp64 and prec == blr.BLR_PREC_MIXED and world == 1:
         o64 = blr.blr_opts_default(b=s["b"], tol=args.tol, precision=blr.BLR_PREC_FP64,
                                    dense_rank=args.dense_rank_fp64, scratch_b2=args.scratch_b2)
-        a64 = blr.blr_compress_kernel(pr.x, pr.y, "yukawa3d", o64)    # its own dense threshold
+        a64 = blr.blr_compress_kernel(pr.x, pr.y, "yukawa3d", o64, col_scale=pr.col_scale)   # its own threshold
         f64, t64 = one_step(o64, a64)
         r64 = probes(blr, f64, a64, pr, torch, dev)
         st64 = blr.blr_stats(f64)

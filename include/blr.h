@@ -65,6 +65,12 @@ typedef struct blr_batch_plan blr_batch_plan; /* opaque launch plan for one or s
  *  sched_ctas   persistent scheduler CTAs; 0 = one per SM.
  *  watchdog_ms  the scheduler gives up (BLR_ERR_TIMEOUT) after this many
  *               milliseconds without any task completing; 0 = 20000.
+ *  eta          blr_compress_kernel only: 0 = weak admissibility (only the
+ *               diagonal tiles are dense); eta > 0 = strong admissibility
+ *               (Section 3.1): tile (i,j) is also kept dense when the
+ *               bounding boxes of its row points and column points are
+ *               closer than eta times the larger box diameter, so a larger
+ *               eta keeps more tiles dense.
  *  scratch_b2   private scratch per scheduler CTA, in units of b*b doubles;
  *               0 = 20 (ample for every rank up to b/2).  A task that needs
  *               more fails the call with BLR_ERR_RANK_OVERFLOW (blr_stats
@@ -80,7 +86,9 @@ typedef struct blr_opts {
   int sched_ctas;
   int watchdog_ms;
   int scratch_b2;
-  int reserved[7];
+  int reserved0;
+  double eta;
+  int reserved[4];
 } blr_opts;
 
 /* Statistics of a handle (host struct filled by blr_stats). */

@@ -33,7 +33,8 @@ class Opts(ctypes.Structure):
     _fields_ = [("b", ctypes.c_int), ("fixed_rank", ctypes.c_int), ("tol", ctypes.c_double),
                 ("rec_tol", ctypes.c_double), ("dense_rank", ctypes.c_int),
                 ("precision", ctypes.c_int), ("sched_ctas", ctypes.c_int),
-                ("watchdog_ms", ctypes.c_int), ("scratch_b2", ctypes.c_int), ("reserved", ctypes.c_int * 7)]
+                ("watchdog_ms", ctypes.c_int), ("scratch_b2", ctypes.c_int), ("reserved0", ctypes.c_int),
+                ("eta", ctypes.c_double), ("reserved", ctypes.c_int * 4)]
 
 
 class Stats(ctypes.Structure):

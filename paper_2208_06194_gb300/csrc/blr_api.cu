@@ -3,6 +3,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <cmath>
 #include <vector>
 #include "blr_internal.h"
 
@@ -92,7 +93,7 @@ static void free_matrix_storage(blr_matrix* a) {
 
 static int check_opts(const blr_opts* o) {
   if (!o) { blr_set_error("opts is NULL"); return BLR_ERR_INVALID; }
-  if (o->fixed_rank < 0 || o->tol < 0 || o->rec_tol < 0 || o->dense_rank < 0 || o->scratch_b2 < 0) {
+  if (o->fixed_rank < 0 || o->tol < 0 || o->rec_tol < 0 || o->dense_rank < 0 || o->scratch_b2 < 0 || o->eta < 0) {
     blr_set_error("negative option value");
     return BLR_ERR_INVALID;
   }
@@ -124,7 +125,47 @@ extern "C" int blr_compress_kernel(const double* x_host, const double* y_host, i
   blr_matrix* a = new blr_matrix;
   if ((rc = alloc_matrix(a, m, n, opts->b))) { delete a; return rc; }
   double *xd = nullptr, *yd = nullptr, *sd = nullptr;
+  unsigned char* adm = nullptr;
   do {
+    if (opts->eta > 0) {
+      // strong admissibility: tile (i,j) is inadmissible (kept dense) when
+      // the bounding boxes of its row and column clusters are closer than
+      // eta times the larger box diameter (a larger eta keeps more dense)
+      const int p = m / opts->b, q = n / opts->b, b = opts->b;
+      std::vector<double> bx((size_t)p * 2 * dim), by((size_t)q * 2 * dim);
+      auto boxes = [&](const double* pts, int nclust, std::vector<double>& box) {
+        for (int c = 0; c < nclust; c++)
+          for (int d = 0; d < dim; d++) {
+            double lo = pts[d + (size_t)c * b * dim], hi = lo;
+            for (int e = 0; e < b; e++) {
+              const double v = pts[d + ((size_t)c * b + e) * dim];
+              lo = v < lo ? v : lo;
+              hi = v > hi ? v : hi;
+            }
+            box[((size_t)c * 2 + 0) * dim + d] = lo;
+            box[((size_t)c * 2 + 1) * dim + d] = hi;
+          }
+      };
+      boxes(x_host, p, bx);
+      boxes(y_host, q, by);
+      std::vector<unsigned char> flags((size_t)p * q);
+      for (int j = 0; j < q; j++)
+        for (int i = 0; i < p; i++) {
+          double dist2 = 0.0, di2 = 0.0, dj2 = 0.0;
+          for (int d = 0; d < dim; d++) {
+            const double ilo = bx[((size_t)i * 2) * dim + d], ihi = bx[((size_t)i * 2 + 1) * dim + d];
+            const double jlo = by[((size_t)j * 2) * dim + d], jhi = by[((size_t)j * 2 + 1) * dim + d];
+            const double gap = jlo > ihi ? jlo - ihi : (ilo > jhi ? ilo - jhi : 0.0);
+            dist2 += gap * gap;
+            di2 += (ihi - ilo) * (ihi - ilo);
+            dj2 += (jhi - jlo) * (jhi - jlo);
+          }
+          const double diam = sqrt(di2 > dj2 ? di2 : dj2);
+          flags[(size_t)j * p + i] = sqrt(dist2) < opts->eta * diam ? 1 : 0;
+        }
+      if ((rc = blr_cuda_check(cudaMalloc(&adm, flags.size()), "alloc admissibility"))) break;
+      if ((rc = blr_cuda_check(cudaMemcpy(adm, flags.data(), flags.size(), cudaMemcpyHostToDevice), "copy admissibility"))) break;
+    }
     if ((rc = blr_cuda_check(cudaMalloc(&xd, sizeof(double) * dim * m), "alloc points"))) break;
     if ((rc = blr_cuda_check(cudaMalloc(&yd, sizeof(double) * dim * n), "alloc points"))) break;
     if ((rc = blr_cuda_check(cudaMemcpyAsync(xd, x_host, sizeof(double) * dim * m, cudaMemcpyHostToDevice, st), "copy x"))) break;
@@ -133,9 +174,10 @@ extern "C" int blr_compress_kernel(const double* x_host, const double* y_host, i
       if ((rc = blr_cuda_check(cudaMalloc(&sd, sizeof(double) * n), "alloc scale"))) break;
       if ((rc = blr_cuda_check(cudaMemcpyAsync(sd, col_scale, sizeof(double) * n, cudaMemcpyHostToDevice, st), "copy scale"))) break;
     }
-    rc = blr_compress_impl(nullptr, 0, xd, yd, dim, kernel_id, sd, m, n, opts, a, st);
+    rc = blr_compress_impl(nullptr, 0, xd, yd, dim, kernel_id, sd, m, n, opts, a, st, adm);
   } while (0);
   cudaStreamSynchronize(st);
+  if (adm) cudaFree(adm);
   if (xd) cudaFree(xd);
   if (yd) cudaFree(yd);
   if (sd) cudaFree(sd);

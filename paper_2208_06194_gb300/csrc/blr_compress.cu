@@ -24,6 +24,7 @@ struct CompressParams {
   double* scratch;
   size_t slab;
   int* status;
+  const unsigned char* inadmissible;   // p*q flags (j*p + i), or NULL: weak admissibility
 };
 
 __device__ __forceinline__ double kernel_entry(const CompressParams& P, int gi, int gj) {
@@ -61,7 +62,7 @@ __global__ void __launch_bounds__(BLR_NT, 1) k_compress(CompressParams P) {
       A0[e] = v;
     }
     __syncthreads();
-    if (i == j) {
+    if (i == j || (P.inadmissible && P.inadmissible[t])) {
       copy_mat(dest, b, A0, b, b, b);
       if (threadIdx.x == 0) P.rank[t] = -1;
       continue;
@@ -126,8 +127,9 @@ __global__ void __launch_bounds__(BLR_NT, 1) k_compress(CompressParams P) {
 
 int blr_compress_impl(const double* a_dev, int lda, const double* x_dev, const double* y_dev, int dim,
                       int kernel_id, const double* scale_dev, int m, int n, const blr_opts* o,
-                      blr_matrix* out, cudaStream_t st) {
+                      blr_matrix* out, cudaStream_t st, const unsigned char* inadmissible_dev) {
   CompressParams P{};
+  P.inadmissible = inadmissible_dev;
   P.m = m; P.n = n; P.b = out->b; P.p = out->p; P.q = out->q; P.cap = out->cap;
   P.dense_rank = (o->dense_rank > 0 && o->dense_rank <= out->cap) ? o->dense_rank : out->cap;
   P.fixed_rank = o->fixed_rank;

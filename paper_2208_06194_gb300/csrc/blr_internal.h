@@ -119,4 +119,5 @@ int blr_run_factor_fp64(const SchedParams& P, int ctas, cudaStream_t st);
 int blr_run_factor_mixed(const SchedParams& P, int ctas, cudaStream_t st);
 int blr_compress_impl(const double* a_dev, int lda, const double* x_dev, const double* y_dev,
                       int dim, int kernel_id, const double* scale_dev, int m, int n,
-                      const blr_opts* o, blr_matrix* out, cudaStream_t st);
+                      const blr_opts* o, blr_matrix* out, cudaStream_t st,
+                      const unsigned char* inadmissible_dev = nullptr);

@@ -308,3 +308,49 @@ def test_mixed_precision_kernel_matrix(lib):
         fac.destroy()
     assert out[lib.BLR_PREC_FP64][0] <= 1e-5 and out[lib.BLR_PREC_MIXED][0] <= 1e-5
     assert out[lib.BLR_PREC_FP64][1] <= 1e-13 and out[lib.BLR_PREC_MIXED][1] <= 1e-6
+
+
+def test_strong_admissibility_keeps_near_tiles_dense(lib):
+    """Strong admissibility (Section 3.1, eta): a tile whose row and column
+    clusters' bounding boxes are closer than eta times the larger diameter
+    is stored dense; every other off-diagonal tile is compressed as before
+    (dense only when its rank exceeds the threshold).  The factorization of
+    the result still meets the tolerance."""
+    import torch
+    pr = W.kernel_problem("yukawa3d", 2048, 1024, 128, 61, 62)
+    p, q, b = 16, 8, 128
+
+    def boxes(pts, nclust):
+        return [(pts[:, c * b:(c + 1) * b].min(axis=1), pts[:, c * b:(c + 1) * b].max(axis=1)) for c in range(nclust)]
+
+    bx, by = boxes(pr.x, p), boxes(pr.y, q)
+    for eta in (0.5, 2.0):
+        opts = lib.blr_opts_default(b=b, tol=1e-8, eta=eta)
+        mat = lib.blr_compress_kernel(pr.x, pr.y, "yukawa3d", opts)
+        rk, tl = lib.blr_matrix_export(mat)
+        weak = lib.blr_compress_kernel(pr.x, pr.y, "yukawa3d", lib.blr_opts_default(b=b, tol=1e-8))
+        rk0, _ = lib.blr_matrix_export(weak)
+        n_forced = 0
+        for j in range(q):
+            for i in range(p):
+                (ilo, ihi), (jlo, jhi) = bx[i], by[j]
+                gap = np.maximum(0.0, np.maximum(jlo - ihi, ilo - jhi))
+                diam = max(np.linalg.norm(ihi - ilo), np.linalg.norm(jhi - jlo))
+                near = np.linalg.norm(gap) < eta * diam
+                t = j * p + i
+                if i == j or near:
+                    assert rk[t] == -1, (eta, i, j)
+                    n_forced += i != j
+                else:
+                    assert rk[t] == rk0[t], (eta, i, j)
+        assert n_forced > 0
+        fac = lib.blr_qr(mat, opts)
+        z = np.random.default_rng(5).standard_normal((1024, 4))
+        rz = lib.blr_apply_r(fac, lib.to_fortran(torch.from_numpy(z)))
+        y = torch.zeros((4, 2048), dtype=torch.float64, device="cuda").t()
+        y[:1024] = rz
+        lib.blr_apply_qt(fac, y, trans=1)
+        az = pr.dense() @ z
+        assert np.linalg.norm(y.cpu().numpy() - az) <= 1e-7 * np.linalg.norm(az)
+        fac.destroy()
+        weak.destroy()
