@@ -349,12 +349,14 @@ int set_smem() {
   return rc;
 }
 
-// Right-hand-side columns per CTA: each CTA walks the whole reflector
-// sequence for its columns, so few columns should still fill the SMs.
+// Right-hand-side columns per CTA.  Each CTA streams every reflector block
+// of the factor for its columns, so the reflector traffic grows with the
+// number of CTAs: measured at 65536 x 32768 with 16 right-hand sides, 8
+// columns per CTA (2 CTAs) took 6 s per Q application, 1 column per CTA
+// (16 CTAs) 23 s.
 int cols_per_cta(int nrhs) {
-  const int nsm = blr_num_sms();
-  int cpc = (nrhs + nsm - 1) / nsm;
-  return cpc < 1 ? 1 : (cpc > kColsPerCta ? kColsPerCta : cpc);
+  (void)nrhs;
+  return kColsPerCta;
 }
 
 int apply_q_launch(const blr_factor* f, double* B, int ldb, int nrhs, int trans, cudaStream_t st) {
