@@ -1,6 +1,6 @@
 """Autotuner of batched factorizations: the tile size b of every matrix and
 the batch's dense threshold, picked by timing candidate configurations on
-this GPU (spec pattern 2).
+this GPU.
 
 For each distinct shape (m, n) of the batch, one representative problem is
 compressed and factored with every candidate tile size b (b must divide m
