@@ -26,6 +26,51 @@ namespace {
 __device__ __forceinline__ double ldg(const double* p) { return __ldcg(p); }
 __device__ __forceinline__ float ldg(const float* p) { return __ldcg(p); }
 
+// FP64 <-> FP32 conversions written from the IEEE 754 binary64 / binary32
+// layouts with integer operations: GB300 runs cvt between the two formats on
+// its reduced FP64 pipe (about one per clock per SM, measured), the integer
+// pipes run these several times faster.  binary64 -> binary32 rounds to
+// nearest with ties away from zero, flushes results below the smallest
+// normal binary32 (2^-126) to zero, and maps overflow to infinity and NaN to
+// NaN; binary32 -> binary64 is exact for normal values and flushes
+// subnormals to zero.  The mixed path's data are far from either limit.
+__device__ __forceinline__ float d2f_bits(double x) {
+  const unsigned long long u = (unsigned long long)__double_as_longlong(x);
+  const unsigned hi = (unsigned)(u >> 32), lo = (unsigned)u;
+  const unsigned s = hi & 0x80000000u, a = hi & 0x7fffffffu;
+  unsigned r;
+  if (a < (897u << 20)) {
+    r = 0u;                                               // below 2^-126: zero
+  } else if (a >= (1151u << 20)) {
+    r = (a > 0x7ff00000u || (a == 0x7ff00000u && lo != 0u)) ? 0x7fc00000u : 0x7f800000u;
+  } else {
+    r = ((a - (896u << 20)) << 3) | (lo >> 29);           // rebias the exponent, keep 23 fraction bits
+    r += (lo >> 28) & 1u;                                 // round (a carry may reach infinity)
+  }
+  return __uint_as_float(s | r);
+}
+
+__device__ __forceinline__ double f2d_bits(float f) {
+  const unsigned u = __float_as_uint(f);
+  const unsigned s = u & 0x80000000u, a = u & 0x7fffffffu;
+  unsigned hi = 0u, lo = 0u;
+  if (a >= 0x7f800000u) {
+    hi = 0x7ff00000u | (a & 0x007fffffu ? 0x00080000u : 0u);   // infinity or a quiet NaN
+  } else if (a >= 0x00800000u) {
+    hi = (a >> 3) + (896u << 20);
+    lo = a << 29;
+  }
+  return __longlong_as_double((long long)(((unsigned long long)(s | hi) << 32) | lo));
+}
+
+template <class To, class From>
+__device__ __forceinline__ To cvt(From x) { return static_cast<To>(x); }
+template <>
+__device__ __forceinline__ float cvt<float, double>(double x) { return d2f_bits(x); }
+template <>
+__device__ __forceinline__ double cvt<double, float>(float x) { return f2d_bits(x); }
+
+
 // Shared-memory carve-out (sizes in doubles; float users reinterpret).
 struct Sm {
   double* pnl;   // BLR_SM_PNL
@@ -149,7 +194,7 @@ __device__ void stage_in(S* dst, int ldd, View<G> src, int rows, int cols) {
     }
 #pragma unroll
     for (int u = 0; u < kMLP; u++)
-      if (base + u * BLR_NT + (int)threadIdx.x < tot) dst[off[u]] = (S)v[u];
+      if (base + u * BLR_NT + (int)threadIdx.x < tot) dst[off[u]] = cvt<S>(v[u]);
   }
 }
 
@@ -159,12 +204,12 @@ __device__ void stage_out(View<G> dst, const S* src, int lds, int rows, int cols
   if (dst.sr == 1) {
     for (int e = threadIdx.x; e < tot; e += BLR_NT) {
       int r = e % rows, c = e / rows;
-      *dst.at(r, c) = (G)src[r + c * lds];
+      *dst.at(r, c) = cvt<G>(src[r + c * lds]);
     }
   } else {
     for (int e = threadIdx.x; e < tot; e += BLR_NT) {
       int c = e % cols, r = e / cols;
-      *dst.at(r, c) = (G)src[r + c * lds];
+      *dst.at(r, c) = cvt<G>(src[r + c * lds]);
     }
   }
 }
@@ -186,7 +231,7 @@ __device__ void copy_mat(D* dst, long long ldd, const Src* src, long long lds, i
     }
 #pragma unroll
     for (int u = 0; u < kMLP; u++)
-      if (base + u * BLR_NT + (int)threadIdx.x < tot) dst[od[u]] = (D)v[u];
+      if (base + u * BLR_NT + (int)threadIdx.x < tot) dst[od[u]] = cvt<D>(v[u]);
   }
 }
 
@@ -384,7 +429,7 @@ __device__ void apply_refl_panel(G* C, long long ldc, int h, int nc, const S* P,
         s += y * W[aa + ll * BLR_NB];
       }
       G* cp = C + row + (long long)(c0 + ll) * ldc;
-      *cp = ldg(cp) - (G)s;
+      *cp = ldg(cp) - cvt<G>(s);
     }
     __syncthreads();
   }
@@ -409,7 +454,7 @@ __device__ void apply_refl_ts(GT* Ct, long long ldt, View<GB> Cb, int ry, int nc
 #pragma unroll
     for (int k = 0; k < KPT; k++) {
       int ll = grp + BLR_NWARP * k;
-      acc[k] = (a < w && ll < cw) ? (S)ldg(Ct + a + (long long)(c0 + ll) * ldt) : S(0);
+      acc[k] = (a < w && ll < cw) ? cvt<S>(ldg(Ct + a + (long long)(c0 + ll) * ldt)) : S(0);
     }
     for (int r0 = 0; r0 < ry; r0 += BLR_RB) {
       const int rb = min(BLR_RB, ry - r0);
@@ -451,7 +496,7 @@ __device__ void apply_refl_ts(GT* Ct, long long ldt, View<GB> Cb, int ry, int nc
     for (int e = threadIdx.x; e < w * cw; e += BLR_NT) {
       int aa = e % w, ll = e / w;
       GT* cp = Ct + aa + (long long)(c0 + ll) * ldt;
-      *cp = ldg(cp) - (GT)W[aa + ll * BLR_NB];
+      *cp = ldg(cp) - cvt<GT>(W[aa + ll * BLR_NB]);
     }
     if (Cb.sr == 1) {
       for (long long e = threadIdx.x; e < (long long)ry * cw; e += BLR_NT) {
@@ -459,7 +504,7 @@ __device__ void apply_refl_ts(GT* Ct, long long ldt, View<GB> Cb, int ry, int nc
         S s = S(0);
         for (int aa = 0; aa < w; aa++) s += Yb[rr + aa * ldyb] * W[aa + ll * BLR_NB];
         GB* cp = Cb.at(rr, c0 + ll);
-        *cp = ldg(cp) - (GB)s;
+        *cp = ldg(cp) - cvt<GB>(s);
       }
     } else {
       for (long long e = threadIdx.x; e < (long long)ry * cw; e += BLR_NT) {
@@ -467,7 +512,7 @@ __device__ void apply_refl_ts(GT* Ct, long long ldt, View<GB> Cb, int ry, int nc
         S s = S(0);
         for (int aa = 0; aa < w; aa++) s += Yb[rr + aa * ldyb] * W[aa + ll * BLR_NB];
         GB* cp = Cb.at(rr, c0 + ll);
-        *cp = ldg(cp) - (GB)s;
+        *cp = ldg(cp) - cvt<GB>(s);
       }
     }
     __syncthreads();
@@ -586,7 +631,7 @@ __device__ int stage_panel(const GY* Y, long long ldy, int m, int c0, int w, con
   S* Ts = as<S>(c.s.t);
   for (int e = threadIdx.x; e < BLR_NB * BLR_NB; e += BLR_NT) {
     int l = e / BLR_NB;
-    Ts[e] = (l < w) ? (S)ldg(Tp + e + (long long)c0 * BLR_NB) : S(0);
+    Ts[e] = (l < w) ? cvt<S>(ldg(Tp + e + (long long)c0 * BLR_NB)) : S(0);
   }
   __syncthreads();
   return ldp;
@@ -813,7 +858,7 @@ __device__ int stage_reflector_panel(View<GY> Yr, int ry, int c0, int w, const G
   S* Ts = as<S>(c.s.t);
   for (int e = threadIdx.x; e < BLR_NB * BLR_NB; e += BLR_NT) {
     int l = e / BLR_NB;
-    Ts[e] = (l < w) ? (S)ldg(Tik + e + (size_t)c0 * BLR_NB) : S(0);
+    Ts[e] = (l < w) ? cvt<S>(ldg(Tik + e + (size_t)c0 * BLR_NB)) : S(0);
   }
   __syncthreads();
   return ldy;

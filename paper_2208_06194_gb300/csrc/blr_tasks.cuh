@@ -333,7 +333,7 @@ __device__ void tsqrt_prep(TaskEnv& env, int i, int k, Ctx& c) {
   // T, block column by block column (X = G(0:J, J) T_J in shared memory)
   for (int e = threadIdx.x; e < b * b; e += BLR_NT) {
     const int a = e % b, l = e / b;
-    T[e] = ((a >> 5) == (l >> 5) && a <= l) ? (float)ldg(Tk + (size_t)l * BLR_NB + (a & 31)) : 0.f;
+    T[e] = ((a >> 5) == (l >> 5) && a <= l) ? cvt<float>(ldg(Tk + (size_t)l * BLR_NB + (a & 31))) : 0.f;
   }
   __syncthreads();
   float* X = tc.buf;                      // top x 32, ld b (the staging area is idle here)
@@ -408,7 +408,7 @@ __device__ void tc_apply_prepared(TaskEnv& env, const float* slot, double* Ct, d
         for (int u = 0; u < 16; u++) ct[u] = (col + u < nn) ? ldg(Ct + a + (size_t)(n0 + col + u) * b) : 0.0;
 #pragma unroll
         for (int u = 0; u < 16; u++)
-          if (col + u < nn) tc_canon_put(zc_h, zc_l, Rp, n0 + col + u, a, v[u] + (float)ct[u]);
+          if (col + u < nn) tc_canon_put(zc_h, zc_l, Rp, n0 + col + u, a, v[u] + cvt<float>(ct[u]));
       });
       PH_END(14);
       }
@@ -437,7 +437,7 @@ __device__ void tc_apply_prepared(TaskEnv& env, const float* slot, double* Ct, d
 #pragma unroll
         for (int u = 0; u < 16; u++) {
           if (col + u < nn) {
-            Ct[a + (size_t)(n0 + col + u) * b] = ct[u] - (double)v[u];
+            Ct[a + (size_t)(n0 + col + u) * b] = ct[u] - cvt<double>(v[u]);
             tc_canon_put(cc_h, cc_l, Rp, n0 + col + u, a, v[u]);    // W as an operand (rows = n, K = a)
           }
         }
@@ -467,7 +467,7 @@ __device__ void tc_apply_prepared(TaskEnv& env, const float* slot, double* Ct, d
         for (int u = 0; u < 16; u++) cb[u] = (col + u < nn) ? ldg(Cb + rr + (size_t)(n0 + col + u) * b) : 0.0;
 #pragma unroll
         for (int u = 0; u < 16; u++)
-          if (col + u < nn) Cb[rr + (size_t)(n0 + col + u) * b] = cb[u] - (double)v[u];
+          if (col + u < nn) Cb[rr + (size_t)(n0 + col + u) * b] = cb[u] - cvt<double>(v[u]);
       });
       PH_END(14);
       }
@@ -752,7 +752,7 @@ __device__ void tc_densify(TaskEnv& env, const double* Tl, int r, double* D, Ctx
     for (int n0 = 0; n0 < b; n0 += 256) {
       const int nn = min(256, b - n0), nn16 = (nn + 15) & ~15;
       tc_epilogue(tc, n0, nn16, [&](int rr, int cc, float v) {
-        if (rr < mrow && cc < nn) D[(r0 + rr) + (size_t)(n0 + cc) * b] = (double)v;
+        if (rr < mrow && cc < nn) D[(r0 + rr) + (size_t)(n0 + cc) * b] = cvt<double>(v);
       });
     }
   }
@@ -769,7 +769,7 @@ __device__ void tc_group_t(const double* Tblk, int wg, const float* Gs, float* T
   for (int e = threadIdx.x; e < 128 * 128; e += BLR_NT) {
     const int a = e & 127, l = e >> 7;
     float v = 0.f;
-    if (a < wg && l < wg && (a >> 5) == (l >> 5) && a <= l) v = (float)ldg(Tblk + (size_t)l * BLR_NB + (a & 31));
+    if (a < wg && l < wg && (a >> 5) == (l >> 5) && a <= l) v = cvt<float>(ldg(Tblk + (size_t)l * BLR_NB + (a & 31)));
     Ts[e] = v;
   }
   __syncthreads();
@@ -831,7 +831,7 @@ __device__ void tc_apply_ts_group(TaskEnv& env, const double* Yg, long long ldy,
     tc_epilogue(tc, n0, nn16, [&](int r, int col, float v) {
       if (r < wg && col < nn) {
         const size_t n = n0 + col;
-        Zs[r + n * 128] = v + (float)ldg(Ct + r + n * ldt);
+        Zs[r + n * 128] = v + cvt<float>(ldg(Ct + r + n * ldt));
       }
     });
   }
@@ -846,7 +846,7 @@ __device__ void tc_apply_ts_group(TaskEnv& env, const double* Yg, long long ldy,
       if (r < wg && col < nn) {
         const size_t n = n0 + col;
         double* p = Ct + r + n * ldt;
-        *p = ldg(p) - (double)v;
+        *p = ldg(p) - cvt<double>(v);
         Zs[r + n * 128] = v;
       }
     });
@@ -863,7 +863,7 @@ __device__ void tc_apply_ts_group(TaskEnv& env, const double* Yg, long long ldy,
       tc_epilogue(tc, n0, nn16, [&](int r, int col, float v) {
         if (r < mrow && col < nn) {
           double* p = Cb + (r0 + r) + (size_t)(n0 + col) * ldb;
-          *p = ldg(p) - (double)v;
+          *p = ldg(p) - cvt<double>(v);
         }
       });
     }

@@ -16,7 +16,7 @@
 // accumulated in FP32, "3xTF32"), which keeps about FP32 accuracy.
 #pragma once
 #include <stdint.h>
-#include "blr_internal.h"
+#include "blr_device.cuh"
 
 #define TC_KC 32                        // K elements per staged chunk
 #define TC_SBO (TC_KC / 4 * 128)        // bytes between 8-row groups of a chunk
@@ -171,7 +171,7 @@ __device__ void tc_stage(float* hi, float* lo, const G* p, long long sr, long lo
       for (int i = 0; i < 4; i++) {
         G v = G(0);
         if (r < nrow && k + i < kmax) v = tc_ld(p + (long long)r * sr + (k + i));
-        tc_split((float)v, h[i], l[i]);
+        tc_split(cvt<float>(v), h[i], l[i]);
       }
       const int off = (rg * TC_SBO + kq * 128 + r8 * 16) >> 2;
       *reinterpret_cast<float4*>(hi + off) = make_float4(h[0], h[1], h[2], h[3]);
@@ -187,7 +187,7 @@ __device__ void tc_stage(float* hi, float* lo, const G* p, long long sr, long lo
       for (int i = 0; i < 4; i++) {
         G v = G(0);
         if (r < nrow && k + i < kmax) v = tc_ld(p + (long long)r * sr + (long long)(k + i) * sc);
-        tc_split((float)v, h[i], l[i]);
+        tc_split(cvt<float>(v), h[i], l[i]);
       }
       const int off = ((r >> 3) * TC_SBO + kq * 128 + (r & 7) * 16) >> 2;
       *reinterpret_cast<float4*>(hi + off) = make_float4(h[0], h[1], h[2], h[3]);
@@ -322,7 +322,7 @@ __device__ void tc_canon(float* hi, float* lo, int R, int K, const G* src, long 
       if (base + u * BLR_NT + (int)threadIdx.x >= groups) continue;
       float h[4], l[4];
 #pragma unroll
-      for (int i = 0; i < 4; i++) tc_split((float)v[u][i], h[i], l[i]);
+      for (int i = 0; i < 4; i++) tc_split(cvt<float>(v[u][i]), h[i], l[i]);
       const size_t off = canon_index(R, rr[u], kk[u]);
       *reinterpret_cast<float4*>(hi + off) = make_float4(h[0], h[1], h[2], h[3]);
       *reinterpret_cast<float4*>(lo + off) = make_float4(l[0], l[1], l[2], l[3]);
