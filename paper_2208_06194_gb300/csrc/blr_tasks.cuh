@@ -53,6 +53,7 @@ struct TaskEnv {
   const TcBulk* tq;   // its bulk-copy pipeline barriers
   const DagShape* dag;
   int skip_succ;      // a successor the task body has already released (-1: none)
+  const float* prep_slot;   // mixed: prepared operands of the current update's low-rank reflector block
   size_t peak;        // high-water mark of used (doubles)
   __device__ double* alloc(size_t n) {
     const size_t nn = (n + 31) & ~(size_t)31;   // 256-byte granules
@@ -304,10 +305,21 @@ __device__ void tsqrt_prep(TaskEnv& env, int i, int k, Ctx& c) {
   float* slot = prep_ptr(P, i, k);
   float *yt_h = slot, *yt_l = slot + op, *yc_h = slot + 2 * op, *yc_l = slot + 3 * op, *tt_h = slot + 4 * op,
         *tt_l = slot + 5 * op;
-  const double* Y = tile_ptr(P, i, k);
+  const int r = ld_rank(rank_ptr(P, i, k));
   const double* Tk = t_ptr(P, i, k);
-  tc_canon(yt_h, yt_l, Rp, b, Y, b, 1, b, b);      // (a, r) = Y[r + a b]
-  tc_canon(yc_h, yc_l, Rp, b, Y, 1, b, b, b);      // (r, a) = Y[r + a b]
+  // the tails: dense Y (b x b) in the tile, or a low-rank tile's Y (r x b)
+  // stored transposed in its V slot; Kt = tail length rounded up to a chunk
+  const int Kt = r < 0 ? b : (r + TC_KC - 1) / TC_KC * TC_KC;
+  if (r < 0) {
+    const double* Y = tile_ptr(P, i, k);
+    tc_canon(yt_h, yt_l, Rp, b, Y, b, 1, b, b);      // (a, s) = Y[s + a b]
+    tc_canon(yc_h, yc_l, Rp, b, Y, 1, b, b, b);      // (s, a) = Y[s + a b]
+  } else {
+    const double* V = tile_ptr(P, i, k) + (size_t)b * P.cap;
+    const int Rs = (r + TC_M - 1) / TC_M * TC_M;
+    tc_canon(yt_h, yt_l, Rp, Kt, V, 1, b, b, r);     // (a, s) = Y(s, a) = V[a + s b]
+    tc_canon(yc_h, yc_l, Rs, b, V, b, 1, r, b);      // (s, a) = V[a + s b]
+  }
   fence_async_global();
   __syncthreads();
   // G = Y^T Y (FP32, ld b, upper block triangle)
@@ -319,7 +331,7 @@ __device__ void tsqrt_prep(TaskEnv& env, int i, int k, Ctx& c) {
       if (n0 + 256 <= m0) continue;       // strictly below the diagonal: not needed
       const int nn = min(256, b - n0), nn16 = (nn + 15) & ~15;
       tc_gemm_bulk(tc, *env.tq, n0, yt_h + (size_t)m0 * TC_KC, yt_l + (size_t)m0 * TC_KC, cs,
-                   yt_h + (size_t)n0 * TC_KC, yt_l + (size_t)n0 * TC_KC, cs, nn16, b / TC_KC);
+                   yt_h + (size_t)n0 * TC_KC, yt_l + (size_t)n0 * TC_KC, cs, nn16, Kt / TC_KC);
     }
     for (int n0 = 0; n0 < b; n0 += 256) {
       if (n0 + 256 <= m0) continue;
@@ -329,7 +341,7 @@ __device__ void tsqrt_prep(TaskEnv& env, int i, int k, Ctx& c) {
       });
     }
   }
-  c.fma += (double)b * b * b / 2;
+  c.fma += (double)b * b * Kt / 2;
   // T, block column by block column (X = G(0:J, J) T_J in shared memory)
   for (int e = threadIdx.x; e < b * b; e += BLR_NT) {
     const int a = e % b, l = e / b;
@@ -480,6 +492,103 @@ __device__ void tc_apply_ts_group(TaskEnv& env, const double* Yg, long long ldy,
                                   double* Ct, long long ldt, double* Cb, long long ldb, int nc, float* Tg,
                                   float* Zs, Ctx& c);
 
+
+// [Ct; Cb] <- Q^T [Ct; Cb] for a LOW-RANK reflector block (tails Y, ry x b,
+// prepared by its TSQRT) with Ct the dense b x b top (FP32, ld b) and Cb the
+// ry x b reduced bottom P = U^T A_ij (FP32, ld ry) of the trapezoidal update:
+// Z = Ct + Y^T Cb, W = T^T Z (the whole block's T), Ct -= W, Cb -= Y W, on
+// the tensor cores.  The same operator as the 32-reflector panel sweep; its
+// products are b x b x ry, b x b x b (triangular) and ry x b x b.
+__device__ void tc_apply_lr_prepared(TaskEnv& env, const float* slot, int ry, float* Ct, float* Cb, Ctx& c) {
+  const SchedParams& P = *env.P;
+  TcCtx& tc = *env.tc;
+  const TcBulk& q = *env.tq;
+  const int b = P.b, Rp = P.prep_rp;
+  const int Kt = (ry + TC_KC - 1) / TC_KC * TC_KC, Rs = (ry + TC_M - 1) / TC_M * TC_M;
+  const size_t op = (size_t)Rp * b, cs = (size_t)Rp * TC_KC, cs_s = (size_t)Rs * TC_KC;
+  const float *yt_h = slot, *yt_l = slot + op, *yc_h = slot + 2 * op, *yc_l = slot + 3 * op, *tt_h = slot + 4 * op,
+              *tt_l = slot + 5 * op;
+  float* pc_h = (float*)env.alloc((size_t)Rp * Kt / 2);   // Cb as an operand (rows = columns n, K = s)
+  float* pc_l = (float*)env.alloc((size_t)Rp * Kt / 2);
+  float* zc_h = (float*)env.alloc(op / 2);                // Z, then W (rows = columns n, K = reflectors)
+  float* zc_l = (float*)env.alloc(op / 2);
+  float* wc_h = (float*)env.alloc(op / 2);
+  float* wc_l = (float*)env.alloc(op / 2);
+  tc_canon(pc_h, pc_l, Rp, Kt, (const float*)Cb, ry, 1, b, ry);      // (n, s) = Cb[s + n ry]
+  fence_async_global();
+  __syncthreads();
+  // Z = Ct + Y^T Cb
+  for (int m0 = 0; m0 < b; m0 += TC_M) {
+    for (int n0 = 0; n0 < b; n0 += 256) {
+      const int nn = min(256, b - n0), nn16 = (nn + 15) & ~15;
+      tc_gemm_bulk(tc, q, n0, yt_h + (size_t)m0 * TC_KC, yt_l + (size_t)m0 * TC_KC, cs, pc_h + (size_t)n0 * TC_KC,
+                   pc_l + (size_t)n0 * TC_KC, cs, nn16, Kt / TC_KC);
+    }
+    for (int n0 = 0; n0 < b; n0 += 256) {
+      const int nn = min(256, b - n0), nn16 = (nn + 15) & ~15;
+      tc_epilogue16(tc, n0, nn16, [&](int r, int col, const float* v) {
+        const int a = m0 + r;
+        if (a >= b) return;
+        float ct[16];
+#pragma unroll
+        for (int u = 0; u < 16; u++) ct[u] = (col + u < nn) ? ldg(Ct + a + (size_t)(n0 + col + u) * b) : 0.f;
+#pragma unroll
+        for (int u = 0; u < 16; u++)
+          if (col + u < nn) tc_canon_put(zc_h, zc_l, Rp, n0 + col + u, a, v[u] + ct[u]);
+      });
+    }
+  }
+  fence_async_global();
+  __syncthreads();
+  // W = T^T Z; Ct -= W
+  for (int m0 = 0; m0 < b; m0 += TC_M) {
+    const int kch = min(b, m0 + TC_M) / TC_KC;
+    for (int n0 = 0; n0 < b; n0 += 256) {
+      const int nn = min(256, b - n0), nn16 = (nn + 15) & ~15;
+      tc_gemm_bulk(tc, q, n0, tt_h + (size_t)m0 * TC_KC, tt_l + (size_t)m0 * TC_KC, cs, zc_h + (size_t)n0 * TC_KC,
+                   zc_l + (size_t)n0 * TC_KC, cs, nn16, kch);
+    }
+    for (int n0 = 0; n0 < b; n0 += 256) {
+      const int nn = min(256, b - n0), nn16 = (nn + 15) & ~15;
+      tc_epilogue16(tc, n0, nn16, [&](int r, int col, const float* v) {
+        const int a = m0 + r;
+        if (a >= b) return;
+        float ct[16];
+#pragma unroll
+        for (int u = 0; u < 16; u++) ct[u] = (col + u < nn) ? ldg(Ct + a + (size_t)(n0 + col + u) * b) : 0.f;
+#pragma unroll
+        for (int u = 0; u < 16; u++) {
+          if (col + u < nn) {
+            Ct[a + (size_t)(n0 + col + u) * b] = ct[u] - v[u];
+            tc_canon_put(wc_h, wc_l, Rp, n0 + col + u, a, v[u]);
+          }
+        }
+      });
+    }
+  }
+  fence_async_global();
+  __syncthreads();
+  // Cb -= Y W
+  for (int m0 = 0; m0 < ry; m0 += TC_M) {
+    for (int n0 = 0; n0 < b; n0 += 256) {
+      const int nn = min(256, b - n0), nn16 = (nn + 15) & ~15;
+      tc_gemm_bulk(tc, q, n0, yc_h + (size_t)m0 * TC_KC, yc_l + (size_t)m0 * TC_KC, cs_s, wc_h + (size_t)n0 * TC_KC,
+                   wc_l + (size_t)n0 * TC_KC, cs, nn16, b / TC_KC);
+    }
+    for (int n0 = 0; n0 < b; n0 += 256) {
+      const int nn = min(256, b - n0), nn16 = (nn + 15) & ~15;
+      tc_epilogue16(tc, n0, nn16, [&](int r, int col, const float* v) {
+        const int s = m0 + r;
+        if (s >= ry) return;
+#pragma unroll
+        for (int u = 0; u < 16; u++)
+          if (col + u < nn) Cb[s + (size_t)(n0 + col + u) * ry] -= v[u];
+      });
+    }
+  }
+  c.fma += 2.0 * b * b * ry + (double)b * b * b / 2;
+}
+
 // TSQRT(i,k): QR([R_kk; A^V_ik]) with A^V = V^T (low-rank) or the dense tile
 // (Section 3.4.3, Eqs. 19-21); Y_ik overwrites A^V in place.  The panel
 // factorization is FP64; the update of the trailing columns runs in S.
@@ -547,7 +656,7 @@ __device__ void task_tsqrt(TaskEnv& env, int i, int k, Ctx& c) {
     }
   }
   if constexpr (std::is_same<S, float>::value) {
-    if (r < 0 && P.prep && env.tc) {
+    if (r != 0 && P.prep && env.tc) {
       // release the next update QR of this column now (it needs only R_kk),
       // then prepare the tensor-core operands for the updates TPMQRT(i,.,k)
       __threadfence();
@@ -684,7 +793,16 @@ __device__ void tpmqrt_core(TaskEnv& env, S* Yt, int rY, const S* Tik, S* Rt, in
     }
   }
   __syncthreads();
-  PH(3, apply_ts_reflector<S>(Yr, ry, b, Tik, Rd, b, colmajor(Pm, ldp), b, true, c));
+  if constexpr (std::is_same<S, float>::value) {
+    if (ylr && env.prep_slot && env.tc) {
+      // low-rank reflector block with prepared tensor-core operands
+      PH(3, tc_apply_lr_prepared(env, env.prep_slot, ry, Rd, Pm, c));
+    } else {
+      PH(3, apply_ts_reflector<S>(Yr, ry, b, Tik, Rd, b, colmajor(Pm, ldp), b, true, c));
+    }
+  } else {
+    PH(3, apply_ts_reflector<S>(Yr, ry, b, Tik, Rd, b, colmajor(Pm, ldp), b, true, c));
+  }
   if (r_scratch) {
     copy_mat(Rt, b, Rd, b, b, b);
     __syncthreads();
@@ -949,6 +1067,8 @@ __device__ void task_tpmqrt(TaskEnv& env, int i, int j, int k, Ctx& c) {
                           rank_ptr(P, k, j), rank_ptr(P, i, j), c));
     return;
   }
+  // a low-rank reflector block whose TSQRT prepared tensor-core operands
+  env.prep_slot = (P.prep && env.tc && rY > 0) ? prep_ptr(P, i, k) : nullptr;
   // mixed: FP32 copies of the operands, FP32 arithmetic, results back to FP64
   float* Yf = (float*)env.alloc((size_t)b * b / 2);
   float* Tf = (float*)env.alloc((size_t)BLR_NB * b / 2);
@@ -1038,7 +1158,7 @@ __global__ void __launch_bounds__(BLR_NT, 1) k_factor(SchedParams P) {
   c.s = sm_carve(smem);
   c.status = P.status;
   DagShape d{P.p, P.q, P.off_larfb, P.off_tsqrt, P.off_tpmqrt};
-  TaskEnv env{&P, P.scratch + (size_t)blockIdx.x * P.slab, 0, false, nullptr, nullptr, &d, -1, 0};
+  TaskEnv env{&P, P.scratch + (size_t)blockIdx.x * P.slab, 0, false, nullptr, nullptr, &d, -1, nullptr, 0};
   const SchedParams* Pm = &P;       // the parameters of the current task's matrix
   constexpr bool kTensor = std::is_same<S, float>::value;
   static_assert(BLR_SMEM_BYTES >= TC_STAGE_BYTES && TC_STAGE_BYTES >= 3 * 128 * 128 * 4, "staging area");
@@ -1102,6 +1222,7 @@ __global__ void __launch_bounds__(BLR_NT, 1) k_factor(SchedParams P) {
     env.used = 0;
     env.overflow = false;
     env.skip_succ = -1;
+    env.prep_slot = nullptr;
     // operand kinds of an update, for the statistics: 4 (Y dense) + 2 (R dense) + (A dense)
     int variant = 0;
     if (type == TASK_TPMQRT && threadIdx.x == 0)
