@@ -54,9 +54,9 @@ def measured_bf16_tflops():
 def roofline(st, k_sec, prec_is_fp64):
     """Roofline of the factorization kernel for its own mix of work.
     FP64: every counted flop on the FP64 ALUs.  Mixed: the updates that run
-    on the tensor cores (a dense reflector block with a dense R_kj or A_ij)
-    at the 3xTF32 rate, every other counted flop at the FP32 SIMT rate; the
-    bound is the sum of the two times and the peak is total flops / bound."""
+    on the tensor cores at the 3xTF32 rate, every other counted flop at the
+    FP32 SIMT rate; the bound is the sum of the two times and the peak is
+    total flops / bound."""
     flops = st["flops"][4]
     achieved = flops / k_sec / 1e12
     if prec_is_fp64:
@@ -66,7 +66,11 @@ def roofline(st, k_sec, prec_is_fp64):
                 "kernel": "k_factor (persistent scheduler)", "flops_counted": flops}
     bf16, src = measured_bf16_tflops()
     p_tc = bf16 * TF32_OVER_BF16 / 3.0
-    f_tc = sum(st["tpmqrt_kind_flops"][v] for v in (5, 6, 7))     # Y~ dense and R_kj or A_ij dense
+    # updates whose reflector block is applied on the tensor cores: Y~ dense
+    # with a dense R_kj or A_ij, and Y~ low-rank with a dense R_kj (their
+    # rounded additions, a small share, are counted at the tensor rate too,
+    # which can only lower the reported fraction)
+    f_tc = sum(st["tpmqrt_kind_flops"][v] for v in (2, 3, 5, 6, 7))
     t_bound = f_tc / (p_tc * 1e12) + (flops - f_tc) / (FP32_PEAK_TFLOPS * 1e12)
     peak = flops / t_bound / 1e12
     return {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": t_bound / k_sec,
@@ -76,7 +80,7 @@ def roofline(st, k_sec, prec_is_fp64):
                           f"SIMT rate ({FP32_PEAK_TFLOPS:.1f} TFLOP/s); peak = flops / summed bound time"),
             "kernel": "k_factor (persistent scheduler)", "flops_counted": flops,
             "tensor_part": {"tflop": f_tc / 1e12,
-                            "cta_seconds": sum(st["tpmqrt_kind_seconds"][v] for v in (5, 6, 7))}}
+                            "cta_seconds": sum(st["tpmqrt_kind_seconds"][v] for v in (2, 3, 5, 6, 7))}}
 
 SIZES = {
     "full": dict(m=65536, n=32768, b=512, seed_x=301, seed_y=302),
