@@ -97,11 +97,12 @@ def parse():
     ap.add_argument("--precision", default="mixed", choices=["fp64", "mixed"])
     ap.add_argument("--tol", type=float, default=1e-5)
     # dense threshold per path (a low-rank result above it is stored dense):
-    # measured best at 65536 x 32768, tol 1e-5 (mixed: 8 4.38 s, 16 4.41, 32 4.85,
-    # 64 5.67, 128 8.63; FP64: 96 57.4 s, 128 51.0, 160 54.8).  The mixed path
-    # runs dense tiles on the tensor cores, low-rank ones as FP32 SIMT code;
-    # 32 = b/16 keeps the low-rank format where it still pays.
-    ap.add_argument("--dense-rank", type=int, default=0, help="0: 32 for mixed, 128 for fp64")
+    # measured best at 65536 x 32768, tol 1e-5.  Mixed: 16 3.57 s, 24 3.71,
+    # 32 3.92, 48 4.25, 64 4.75 (dense and low-rank-reflector updates with a
+    # dense R run on the tensor cores, the other low-rank work as FP32 SIMT
+    # code, so dense pays from low ranks on).  FP64: 96 57.4 s, 128 51.0,
+    # 160 54.8.
+    ap.add_argument("--dense-rank", type=int, default=0, help="0: 16 for mixed, 128 for fp64")
     ap.add_argument("--dense-rank-fp64", type=int, default=128)
     ap.add_argument("--size", default="full", choices=list(SIZES))
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
@@ -408,7 +409,7 @@ def run_batched(args, rank, world):
 def main():
     args = parse()
     if args.dense_rank == 0:
-        args.dense_rank = 32 if args.precision == "mixed" else 128
+        args.dense_rank = 16 if args.precision == "mixed" else 128
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", str(args.gpus)))
     local = int(os.environ.get("LOCAL_RANK", "0"))
