@@ -1,6 +1,8 @@
-// Host side of blr_qr: builds the scheduler state of the tile DAG of
-// Algorithm 4 and launches the persistent kernel (blr_factor_fp64.cu,
-// blr_factor_mixed.cu); plus the host-only check of the DAG formulas.
+// Host side of blr_qr and blr_qr_batched: builds the scheduler state of the
+// tile DAGs of Algorithm 4 (one or several matrices), launches the
+// persistent kernel (blr_factor_fp64.cu, blr_factor_mixed.cu) and reads its
+// status back; the capturable launch plans; and the host-only check of the
+// DAG formulas.
 #include <cstdio>
 #include <cstdlib>
 #include <algorithm>

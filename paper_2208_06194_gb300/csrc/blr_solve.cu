@@ -1,8 +1,9 @@
 // Uses of the factor: Q^T B and Q B (Algorithm 5, reflectors applied exactly
-// in factorization order or its reverse), R X, A~ X, and least squares
-// x = R^{-1} (Q^T B)(1:n) with optional refinement (QR for least squares,
-// Section 1).  Every kernel gives each CTA a group of right-hand-side
-// columns; the reflector sequence is applied in order inside the CTA.
+// in factorization order or its reverse), R X, R^{-1} C, R^{-T} C, A~ X,
+// least squares x = R^{-1} (Q^T B)(1:n) with optional refinement (QR for
+// least squares, Section 1) and its adjoint.  Every kernel gives each CTA a
+// group of right-hand-side columns; the reflector sequence is applied in
+// order inside the CTA.
 #include <cstdio>
 #include <vector>
 #include "blr_device.cuh"
@@ -349,15 +350,12 @@ int set_smem() {
   return rc;
 }
 
-// Right-hand-side columns per CTA.  Each CTA streams every reflector block
-// of the factor for its columns, so the reflector traffic grows with the
-// number of CTAs: measured at 65536 x 32768 with 16 right-hand sides, 8
-// columns per CTA (2 CTAs) took 6 s per Q application, 1 column per CTA
-// (16 CTAs) 23 s.
-int cols_per_cta(int nrhs) {
-  (void)nrhs;
-  return kColsPerCta;
-}
+// Right-hand-side columns per CTA (kColsPerCta).  Each CTA streams every
+// reflector block of the factor for its columns, so the reflector traffic
+// grows with the number of CTAs: measured at 65536 x 32768 with 16
+// right-hand sides, 8 columns per CTA (2 CTAs) took 6 s per Q application,
+// 1 column per CTA (16 CTAs) 23 s.
+int cols_per_cta(int) { return kColsPerCta; }
 
 int apply_q_launch(const blr_factor* f, double* B, int ldb, int nrhs, int trans, cudaStream_t st) {
   FactorView F{};
