@@ -341,6 +341,17 @@ void blr_destroy_factor(blr_factor* f);
 int blr_dag_selfcheck(int p, int q, unsigned seed);
 
 /*
+ * blr_batch_selfcheck -- host only, no device work: the tile DAGs of count
+ * matrices of p[t] x q[t] tiles numbered consecutively as a batched launch
+ * numbers them, each task located the way the scheduler kernel locates it,
+ * and the dependency-counter protocol run over the whole batch in a seeded
+ * random order.  Returns 0 when every task runs exactly once after its
+ * predecessors and no dependency crosses matrices; a positive code
+ * otherwise (100: bad shapes).
+ */
+int blr_batch_selfcheck(const int* p, const int* q, int count, unsigned seed);
+
+/*
  * blr_tc_gemm_selftest -- D = A B (device, column-major, FP64 in and out:
  * A m x k, lda >= m; B k x n, ldb >= k; D m x n, ldd >= m) through the
  * tensor-core building block of the mixed-precision updates (tcgen05 TF32

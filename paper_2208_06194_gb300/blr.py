@@ -83,6 +83,7 @@ _SIGS = {
     "blr_destroy_matrix": (None, [_P]),
     "blr_destroy_factor": (None, [_P]),
     "blr_dag_selfcheck": (_I, [_I, _I, ctypes.c_uint]),
+    "blr_batch_selfcheck": (_I, [_IP, _IP, _I, ctypes.c_uint]),
     "blr_tc_gemm_selftest": (_I, [_P, _I, _P, _I, _P, _I, _I, _I, _I, _P]),
 }
 EXPORTED = tuple(_SIGS)
@@ -391,6 +392,13 @@ def blr_stats(obj) -> dict:
     for k in ("tpmqrt_kind", "tpmqrt_kind_seconds", "tpmqrt_kind_flops"):
         d[k] = list(getattr(s, k))
     return d
+
+
+def blr_batch_selfcheck(ps, qs, seed: int = 0) -> int:
+    """Host-only check of a batch's task numbering and protocol (0 = pass)."""
+    p = np.ascontiguousarray(ps, dtype=np.int32)
+    q = np.ascontiguousarray(qs, dtype=np.int32)
+    return lib().blr_batch_selfcheck(p.ctypes.data_as(_IP), q.ctypes.data_as(_IP), len(p), seed)
 
 
 def blr_dag_selfcheck(p: int, q: int, seed: int = 0) -> int:

@@ -109,6 +109,19 @@ BLR_HD int dag_queue(int type, int i, int j, int k) {
   return 2;
 }
 
+// A batch numbers the tasks of several matrices consecutively: matrix t's
+// tasks are [base[t], base[t+1]).  Returns the matrix of a batch-wide task id
+// (nmat >= 1, base[0] = 0 <= task < base[nmat]).
+BLR_HD int dag_find_matrix(const int* base, int nmat, int task) {
+  int lo = 0, hi = nmat - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (base[mid] <= task) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
 // Fills the offset tables (q+1 entries each) and returns the task count.
 BLR_HD int dag_offsets(int p, int q, int* off_larfb, int* off_tsqrt, int* off_tpmqrt) {
   int id = q;

@@ -352,6 +352,63 @@ extern "C" const blr_factor* blr_batch_plan_factor(const blr_batch_plan* plan, i
 
 extern "C" void blr_batch_plan_destroy(blr_batch_plan* plan) { plan_free(plan); }
 
+// Host-side check of a batch's task numbering (no device work): the DAGs of
+// matrices of shapes (p[t], q[t]) numbered consecutively as a launch plan
+// does, every task located by dag_find_matrix as the scheduler kernel does,
+// and the dependency-counter protocol run over the whole batch in a seeded
+// random order, releasing successors at task_base + local id.  Checks that
+// every task runs once, after all its predecessors, that tasks of different
+// matrices never depend on each other, and that each matrix's GEQRT(0) is
+// the only initially ready task of that matrix.  0 on success.
+extern "C" int blr_batch_selfcheck(const int* p, const int* q, int count, unsigned seed) {
+  if (!p || !q || count < 1) return 100;
+  std::vector<int> base(count + 1, 0);
+  std::vector<std::vector<int>> offL(count), offS(count), offP(count);
+  for (int t = 0; t < count; t++) {
+    if (p[t] < 1 || q[t] < 1 || q[t] > p[t]) return 100;
+    offL[t].resize(q[t] + 1); offS[t].resize(q[t] + 1); offP[t].resize(q[t] + 1);
+    base[t + 1] = base[t] + dag_offsets(p[t], q[t], offL[t].data(), offS[t].data(), offP[t].data());
+  }
+  const int n = base[count];
+  std::vector<int> deps(n, 0), runs(n, 0);
+  auto shape = [&](int t) { return DagShape{p[t], q[t], offL[t].data(), offS[t].data(), offP[t].data()}; };
+  for (int id = 0; id < n; id++) {
+    const int t = dag_find_matrix(base.data(), count, id);
+    if (id < base[t] || id >= base[t + 1]) return 1;
+    const DagShape d = shape(t);
+    int i, j, k;
+    const int ty = dag_decode(d, id - base[t], &i, &j, &k);
+    if (ty < 0) return 2;
+    deps[id] = dag_indegree(ty, i, j, k);
+    if ((deps[id] == 0) != (id == base[t])) return 3;          // only GEQRT(0) starts ready
+  }
+  std::vector<int> ready;
+  for (int t = 0; t < count; t++) ready.push_back(base[t]);
+  unsigned st = seed * 2654435761u + 7u;
+  int executed = 0;
+  while (!ready.empty()) {
+    st = st * 1664525u + 1013904223u;
+    const size_t pick = st % ready.size();
+    const int id = ready[pick];
+    ready[pick] = ready.back();
+    ready.pop_back();
+    if (deps[id] != 0 || runs[id]++) return 4;
+    executed++;
+    const int t = dag_find_matrix(base.data(), count, id);
+    const DagShape d = shape(t);
+    int i, j, k;
+    const int ty = dag_decode(d, id - base[t], &i, &j, &k);
+    int bad = 0;
+    dag_for_each_successor(d, ty, i, j, k, [&](int sid) {
+      const int gid = base[t] + sid;
+      if (gid < base[t] || gid >= base[t + 1]) bad = 1;          // stays inside its matrix
+      else if (--deps[gid] == 0) ready.push_back(gid);
+    });
+    if (bad) return 5;
+  }
+  return executed == n ? 0 : 6;
+}
+
 // Host-side check of the DAG formulas (no device work): builds the DAG from
 // dag_successors, checks every in-degree against dag_indegree, and runs the
 // counter protocol in a seeded random order, checking that each task runs

@@ -1210,7 +1210,7 @@ __global__ void __launch_bounds__(BLR_NT, 1) k_factor(SchedParams P) {
         if (__ldg(P.mat_base + mid) <= task) lo = mid;
         else hi = mid - 1;
       }
-      Pm = P.mats + lo;
+      Pm = P.mats + lo;   // the search of dag_find_matrix (blr_dag.h), checked on the host by blr_batch_selfcheck
       d = DagShape{Pm->p, Pm->q, Pm->off_larfb, Pm->off_tsqrt, Pm->off_tpmqrt};
       env.P = Pm;
     }

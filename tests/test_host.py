@@ -47,3 +47,15 @@ def test_dag_formulas_host_selfcheck(built, p, q):
 
 def test_dag_selfcheck_rejects_bad_shape(built):
     assert blr.blr_dag_selfcheck(2, 3, 0) != 0
+
+
+@pytest.mark.parametrize("shapes", [[(1, 1)], [(3, 2), (8, 4)], [(16, 8), (5, 5), (2, 1), (64, 32)],
+                                    [(12, 6)] * 7])
+def test_batch_task_numbering_host_selfcheck(built, shapes):
+    ps, qs = zip(*shapes)
+    for seed in range(3):
+        assert blr.blr_batch_selfcheck(ps, qs, seed) == 0
+
+
+def test_batch_selfcheck_rejects_bad_shapes(built):
+    assert blr.blr_batch_selfcheck([2, 3], [1, 4], 0) != 0
