@@ -20,6 +20,9 @@ Low-Rank Matrices"):
   (3.4.4), with a recompression after every low-rank sum (Section 3.1).
 * Left multiplication by Q and Q^T in the tiled order (Algorithm 5, read
   with the "I -" that the printed update omits).
+* The blocked (block-column) Householder BLR-QR of Section 3.3: Householder
+  QR of each stacked block column of A^V blocks (Eqs. 13-17) and the
+  block-column reflector applied to the columns on its right (Eq. 18).
 * Res and Orth of Section 5.
 
 Readings where the paper is silent (the same list is kept in the design
@@ -400,6 +403,121 @@ def blr_qr(a: BLRMatrix, eps: float) -> Factor:
                 tl[k][j], tl[i][j] = tpmqrt(tl[i][k], tik, tl[k][j], tl[i][j], eps, cap)
         tl[k][k] = dense_tile(np.triu(rkk) + np.tril(ykk, -1))
     return Factor(p, q, b, tl, ts)
+
+
+# ----------------------------------------------------------------------------
+# Blocked Householder BLR-QR (Section 3.3; Algorithm 2 on a BLR matrix)
+# ----------------------------------------------------------------------------
+
+
+def block_column_qr(col: list):
+    """Triangularization of a block column (Section 3.3.1, Eqs. 13-17):
+    Householder QR of the stacked A^V_ik (the dense block, or V^T of a
+    low-rank block; the diagonal block is dense), i = k..p-1.
+
+    Returns R_kk (b x b upper), the tails Y~_ik = A^U_ik Y_ik as tiles
+    (low-rank (U_ik, Y_ik^T) where A_ik is low-rank, dense otherwise; the
+    diagonal one unit lower triangular) and T_k (b x b upper) with
+    Q_k = I - Y~ T_k Y~^T over the stacked rows of the column."""
+    parts = [t.d if t.kind == "D" else t.v.T for t in col]
+    rows = [p.shape[0] for p in parts]
+    s = np.vstack(parts).astype(np.float64, copy=True)
+    nb = s.shape[1]
+    y = np.zeros_like(s)
+    tau = np.zeros(nb)
+    for j in range(nb):
+        beta, tj, v = reflector(s[j:, j])
+        s[j:, j + 1:] -= tj * np.outer(v, v @ s[j:, j + 1:])
+        s[j, j] = beta
+        s[j + 1:, j] = 0.0
+        y[j:, j] = v
+        tau[j] = tj
+    t = t_from_gram(y.T @ y, tau)
+    tails, r0 = [], 0
+    for tile, nr in zip(col, rows):
+        yi = y[r0:r0 + nr]
+        tails.append(Tile("L", u=tile.u, v=yi.T.copy()) if tile.kind == "L" else dense_tile(yi))
+        r0 += nr
+    return np.triu(s[:nb]), tails, t
+
+
+def apply_block_column_reflector(tails: list, t: np.ndarray, col: list, eps: float, cap: int) -> list:
+    """Q_k^T applied to a block column (Section 3.3.2, Eq. 18):
+    S = sum_i Y~_ik^T A_ij (products OP3/OP4, rounded additions),
+    W = T_k^T S, A_ij <- A_ij - Y~_ik W (each difference a rounded addition)."""
+    s = None
+    for yt, a in zip(tails, col):
+        x = mul(transpose(yt), a)
+        s = x if s is None else add(s, x, eps, cap)
+    w = left_dense(t.T, s)
+    return [add(a, neg(mul(yt, w)), eps, cap) for yt, a in zip(tails, col)]
+
+
+@dataclasses.dataclass
+class BlockedFactor:
+    """Blocked factor: r[k][j] (j >= k) the tiles of R; y[k] the tails of
+    block column k (rows k..p-1); t[k] its T_k."""
+
+    p: int
+    q: int
+    b: int
+    r: dict
+    y: list
+    t: list
+
+    def r_dense(self) -> np.ndarray:
+        b, n = self.b, self.q * self.b
+        out = np.zeros((n, n))
+        for (k, j), tile in self.r.items():
+            out[k * b:(k + 1) * b, j * b:(j + 1) * b] = np.triu(tile.dense()) if j == k else tile.dense()
+        return out
+
+    def y_stacked(self, k: int) -> np.ndarray:
+        """Y~ of block column k as a dense (m - k b) x b matrix."""
+        return np.vstack([yt.dense() for yt in self.y[k]])
+
+
+def blr_qr_blocked(a: BLRMatrix, eps: float) -> BlockedFactor:
+    """Blocked Householder BLR-QR: for each block column, triangularize it
+    (block_column_qr), then apply its reflector to every block column on
+    its right (apply_block_column_reflector)."""
+    p, q, b, cap = a.p, a.q, a.b, a.cap
+    tl = [[t.copy() for t in row] for row in a.tiles]
+    r, ys, ts = {}, [], []
+    for k in range(q):
+        col = [tl[i][k] for i in range(k, p)]
+        if col[0].kind != "D":
+            col[0] = dense_tile(col[0].dense())
+        rkk, tails, tk = block_column_qr(col)
+        r[(k, k)] = dense_tile(rkk)
+        ys.append(tails)
+        ts.append(tk)
+        for j in range(k + 1, q):
+            new = apply_block_column_reflector(tails, tk, [tl[i][j] for i in range(k, p)], eps, cap)
+            for i, tile in zip(range(k, p), new):
+                tl[i][j] = tile
+            r[(k, j)] = tl[k][j]
+    return BlockedFactor(p, q, b, r, ys, ts)
+
+
+def blocked_apply_qt(f: BlockedFactor, c: np.ndarray) -> np.ndarray:
+    """Q^T C for the blocked factor, block columns in order."""
+    b = f.b
+    c = np.array(c, dtype=np.float64, copy=True)
+    for k in range(f.q):
+        yk = f.y_stacked(k)
+        c[k * b:] -= yk @ (f.t[k].T @ (yk.T @ c[k * b:]))
+    return c
+
+
+def blocked_apply_q(f: BlockedFactor, c: np.ndarray) -> np.ndarray:
+    """Q C for the blocked factor, block columns in reverse order."""
+    b = f.b
+    c = np.array(c, dtype=np.float64, copy=True)
+    for k in reversed(range(f.q)):
+        yk = f.y_stacked(k)
+        c[k * b:] -= yk @ (f.t[k] @ (yk.T @ c[k * b:]))
+    return c
 
 
 # ----------------------------------------------------------------------------

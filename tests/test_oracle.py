@@ -346,3 +346,74 @@ def test_ill_conditioned_scale():
     d = W.ill_conditioned_scale(11)
     assert d[0] == 1.0 and np.isclose(d[-1], 1e-10)
     assert np.allclose(d[1:] / d[:-1], 10 ** (-1.0))
+
+
+# ---------------------------------------------------------------- blocked variant (Section 3.3)
+
+@pytest.mark.parametrize("m,n,b", [(32, 16, 4), (48, 24, 8)])
+def test_blocked_full_rank_equals_dense_qr(m, n, b):
+    """Dense tiles everywhere: the block-column QR is the textbook QR of the
+    whole matrix (QR uniqueness up to row signs)."""
+    a = np.random.default_rng(m + 1).standard_normal((m, n))
+    blr = O.compress(tiles_of(a, b), m // b, n // b, b, eps=0.0)
+    f = O.blr_qr_blocked(blr, 0.0)
+    r_dense, _ = D.householder_qr(a)
+    assert np.allclose(D.sign_normalize(f.r_dense()), D.sign_normalize(r_dense), atol=1e-13 * np.abs(r_dense).max())
+
+
+@pytest.mark.parametrize("m,n,b,k", [(128, 64, 16, 2), (96, 48, 8, 1)])
+def test_blocked_exact_low_rank_matches_dense_and_tiled(m, n, b, k):
+    """Exact rank-k tiles: the blocked variant gives the dense QR's R (up to
+    row signs), the same R as the tiled Algorithm 4, an orthogonal Q and
+    Q^T A = [R; 0]."""
+    a = W.random_blr_dense(m, n, b, k, seed=m + 2 * k)
+    blr = O.compress(tiles_of(a, b), m // b, n // b, b, eps=1e-14)
+    fb = O.blr_qr_blocked(blr, 1e-15)
+    ft = O.blr_qr(blr, 1e-15)
+    rb = D.sign_normalize(fb.r_dense())
+    assert np.linalg.norm(rb - D.sign_normalize(np.linalg.qr(a, mode="r"))) <= 1e-12 * np.linalg.norm(rb)
+    assert np.linalg.norm(rb - D.sign_normalize(ft.r_dense())) <= 1e-12 * np.linalg.norm(rb)
+    e = np.zeros((m, n))
+    e[:n] = np.eye(n)
+    q1 = O.blocked_apply_q(fb, e)
+    assert np.linalg.norm(q1.T @ q1 - np.eye(n)) / np.sqrt(n) < 1e-13
+    qta = O.blocked_apply_qt(fb, a)
+    assert np.linalg.norm(qta[:n] - fb.r_dense()) <= 1e-12 * np.linalg.norm(a)
+    assert np.linalg.norm(qta[n:]) <= 1e-12 * np.linalg.norm(a)
+
+
+def test_blocked_tails_keep_the_blr_structure():
+    """Y~_ik = A^U_ik Y_ik (Section 3.3.1): low-rank with A_ik's own U where
+    A_ik is low-rank (checked on the first block column, before any update
+    changes the tiles; later ones may have become dense through rank growth),
+    an orthonormal U wherever it is low-rank, and a unit lower triangular
+    tail in the diagonal block."""
+    m, n, b, k = 64, 32, 8, 2
+    a = W.random_blr_dense(m, n, b, k, seed=5)
+    blr = O.compress(tiles_of(a, b), m // b, n // b, b, eps=1e-14)
+    f = O.blr_qr_blocked(blr, 1e-15)
+    for kk in range(n // b):
+        for off, yt in enumerate(f.y[kk]):
+            i = kk + off
+            if i == kk:
+                assert yt.kind == "D" and np.allclose(np.triu(yt.d), np.eye(b))
+                continue
+            if kk == 0:                       # the input's low-rank tiles
+                assert yt.kind == "L" and np.array_equal(yt.u, blr.tiles[i][0].u)
+            if yt.kind == "L":                # later columns: tiles the updates left low-rank
+                assert np.allclose(yt.u.T @ yt.u, np.eye(yt.u.shape[1]), atol=1e-12)
+                assert yt.v.shape == (b, yt.u.shape[1])
+
+
+def test_blocked_with_truncation_meets_the_tolerance():
+    """A kernel matrix compressed at 1e-8 and factored with rounded
+    additions at 1e-8: Res against A~ at the tolerance level, Q orthogonal."""
+    pr = W.kernel_problem("yukawa3d", 256, 128, 32, 71, 72)
+    blr = O.compress(pr.tile, 8, 4, 32, eps=1e-8)
+    f = O.blr_qr_blocked(blr, 1e-8)
+    at = blr.dense()
+    e = np.zeros((256, 128))
+    e[:128] = np.eye(128)
+    q1 = O.blocked_apply_q(f, e)
+    assert np.linalg.norm(q1 @ f.r_dense() - at) <= 10 * 1e-8 * np.linalg.norm(at)
+    assert np.linalg.norm(q1.T @ q1 - np.eye(128)) / np.sqrt(128) < 1e-12
