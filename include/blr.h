@@ -18,8 +18,10 @@
  *    because each reads back a device status word.
  *  - Handles (blr_matrix, blr_factor) own device memory allocated by the
  *    library; the caller owns every buffer it passes in.
+ *  - Pointers, sizes and options are checked on the host before any CUDA
+ *    call: a bad argument gives BLR_ERR_INVALID on any machine.
  *  - Nothing here falls back to the CPU: without a usable CUDA device every
- *    call fails with BLR_ERR_CUDA.
+ *    call with valid arguments fails with BLR_ERR_CUDA.
  */
 #ifndef BLR_H
 #define BLR_H
@@ -226,6 +228,9 @@ int blr_qr_batched(blr_matrix** a, int count, const blr_opts* opts, blr_factor**
  *                         content is the last finished launch's), usable
  *                         with every function taking a const blr_factor*.
  * Calls on one plan must not overlap on the GPU.
+ * Errors of blr_batch_plan_create: BLR_ERR_INVALID (NULL array or plan,
+ * count < 1, a NULL matrix, options blr_qr rejects), BLR_ERR_OOM,
+ * BLR_ERR_CUDA; on error *plan is NULL and nothing stays allocated.
  */
 int blr_batch_plan_create(blr_matrix* const* a, int count, const blr_opts* opts, blr_batch_plan** plan,
                           void* stream);

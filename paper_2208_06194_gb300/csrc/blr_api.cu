@@ -114,13 +114,13 @@ extern "C" int blr_compress_kernel(const double* x_host, const double* y_host, i
   int rc;
   if (!out || !x_host || !y_host) { blr_set_error("NULL argument"); return BLR_ERR_INVALID; }
   *out = nullptr;
-  if ((rc = check_device())) return rc;
   if ((rc = check_opts(opts))) return rc;
   if ((rc = check_shape(m, n, opts->b))) return rc;
   if (kernel_id < 0 || kernel_id > 2) { blr_set_error("unknown kernel id %d", kernel_id); return BLR_ERR_INVALID; }
   const int want_dim = kernel_id == BLR_KERNEL_INV1D ? 1 : 3;
   if (dim != want_dim) { blr_set_error("kernel %d needs dim=%d, got %d", kernel_id, want_dim, dim); return BLR_ERR_INVALID; }
   if (opts->fixed_rank > opts->b / 2) { blr_set_error("fixed_rank must be <= b/2"); return BLR_ERR_INVALID; }
+  if ((rc = check_device())) return rc;
   cudaStream_t st = (cudaStream_t)stream;
   blr_matrix* a = new blr_matrix;
   if ((rc = alloc_matrix(a, m, n, opts->b))) { delete a; return rc; }
@@ -191,11 +191,11 @@ extern "C" int blr_compress_dense(const double* a_dev, int lda, int m, int n, co
   int rc;
   if (!out || !a_dev) { blr_set_error("NULL argument"); return BLR_ERR_INVALID; }
   *out = nullptr;
-  if ((rc = check_device())) return rc;
   if ((rc = check_opts(opts))) return rc;
   if ((rc = check_shape(m, n, opts->b))) return rc;
   if (lda < m) { blr_set_error("lda=%d < m=%d", lda, m); return BLR_ERR_INVALID; }
   if (opts->fixed_rank > opts->b / 2) { blr_set_error("fixed_rank must be <= b/2"); return BLR_ERR_INVALID; }
+  if ((rc = check_device())) return rc;
   blr_matrix* a = new blr_matrix;
   if ((rc = alloc_matrix(a, m, n, opts->b))) { delete a; return rc; }
   rc = blr_compress_impl(a_dev, lda, nullptr, nullptr, 0, 0, nullptr, m, n, opts, a, (cudaStream_t)stream);
@@ -209,7 +209,6 @@ static int import_tiles(int m, int n, int b, const int* ranks_host, const double
   int rc;
   if (!out || !ranks_host || !tiles_host) { blr_set_error("NULL argument"); return BLR_ERR_INVALID; }
   *out = nullptr;
-  if ((rc = check_device())) return rc;
   if ((rc = check_shape(m, n, b))) return rc;
   const int p = m / b, q = n / b;
   for (int t = 0; t < p * q; t++) {
@@ -218,6 +217,7 @@ static int import_tiles(int m, int n, int b, const int* ranks_host, const double
       return BLR_ERR_INVALID;
     }
   }
+  if ((rc = check_device())) return rc;
   blr_matrix* a = new blr_matrix;
   if ((rc = alloc_matrix(a, m, n, b))) { delete a; return rc; }
   cudaStream_t st = (cudaStream_t)stream;
@@ -268,7 +268,7 @@ extern "C" int blr_matrix_clone(const blr_matrix* a, blr_matrix** out, void* str
   return BLR_OK;
 }
 
-static int check_qr_opts(const blr_opts* opts) {
+int blr_check_qr_opts(const blr_opts* opts) {
   if (!opts) { blr_set_error("opts is NULL"); return BLR_ERR_INVALID; }
   if (opts->rec_tol < 0 || (opts->rec_tol == 0 && opts->tol <= 0)) {
     blr_set_error("blr_qr needs rec_tol > 0 or tol > 0");
@@ -313,7 +313,7 @@ extern "C" int blr_qr(blr_matrix* a, const blr_opts* opts, blr_factor** f, void*
   int rc;
   if (!a || !f) { blr_set_error("NULL argument"); return BLR_ERR_INVALID; }
   *f = nullptr;
-  if ((rc = check_qr_opts(opts))) { free_matrix_storage(a); delete a; return rc; }
+  if ((rc = blr_check_qr_opts(opts))) { free_matrix_storage(a); delete a; return rc; }
   blr_factor* F = nullptr;
   if ((rc = factor_adopt(a, opts, &F))) return rc;
   rc = blr_launch_factor(F, opts, (cudaStream_t)stream);
@@ -327,7 +327,7 @@ extern "C" int blr_qr(blr_matrix* a, const blr_opts* opts, blr_factor** f, void*
 
 extern "C" int blr_qr_batched(blr_matrix** a, int count, const blr_opts* opts, blr_factor** f, void* stream) {
   if (!a || !f || count < 1) { blr_set_error("NULL argument or count < 1"); return BLR_ERR_INVALID; }
-  int rc = check_qr_opts(opts);
+  int rc = blr_check_qr_opts(opts);
   for (int m = 0; m < count && !rc; m++)
     if (!a[m]) { blr_set_error("matrix %d is NULL", m); rc = BLR_ERR_INVALID; }
   std::vector<blr_factor*> fs;

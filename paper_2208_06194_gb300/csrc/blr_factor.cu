@@ -315,8 +315,11 @@ extern "C" int blr_batch_plan_create(blr_matrix* const* a, int count, const blr_
                                      void* stream) {
   if (!a || !opts || !out || count < 1) { blr_set_error("NULL argument or count < 1"); return BLR_ERR_INVALID; }
   *out = nullptr;
+  int rc = blr_check_qr_opts(opts);
+  if (rc) return rc;
+  for (int m = 0; m < count; m++)
+    if (!a[m]) { blr_set_error("matrix %d is NULL", m); return BLR_ERR_INVALID; }
   std::vector<blr_factor*> fs;
-  int rc = BLR_OK;
   for (int m = 0; m < count && !rc; m++) {
     blr_factor* f = nullptr;
     rc = blr_factor_alloc_like(a[m], opts, &f);

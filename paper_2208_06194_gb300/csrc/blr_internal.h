@@ -114,6 +114,9 @@ int blr_num_sms();
 // kernel launchers implemented in the .cu files
 int blr_launch_factor(blr_factor* f, const blr_opts* o, cudaStream_t st);
 int blr_launch_factors(blr_factor* const* fs, int count, const blr_opts* o, cudaStream_t st);
+// Options check shared by blr_qr, blr_qr_batched and blr_batch_plan_create
+// (host only: BLR_ERR_INVALID with a message, no CUDA call).
+int blr_check_qr_opts(const blr_opts* opts);
 int blr_factor_alloc_like(const blr_matrix* a, const blr_opts* opts, blr_factor** out);
 int blr_run_factor_fp64(const SchedParams& P, int ctas, cudaStream_t st);
 int blr_run_factor_mixed(const SchedParams& P, int ctas, cudaStream_t st);
