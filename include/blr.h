@@ -357,6 +357,18 @@ int blr_dag_selfcheck(int p, int q, unsigned seed);
 int blr_batch_selfcheck(const int* p, const int* q, int count, unsigned seed);
 
 /*
+ * blr_dag_task -- host only, no device work: task `id` of the p x q tile DAG
+ * of Algorithm 4 as the device scheduler numbers and releases it (the
+ * formulas the scheduler kernel runs).  task[0..3] (host, 4 ints) receives
+ * the type (0 GEQRT, 1 LARFB, 2 TSQRT, 3 TPMQRT) and the 0-based tile
+ * indices i, j, k; succ (host, cap ints, cap >= q + 1) receives the ids of
+ * the tasks it releases.  Returns the number of successors, or -1 (message
+ * in blr_last_error) for q > p, p or q < 1, an id outside the DAG, NULL
+ * pointers or cap < q + 1.
+ */
+int blr_dag_task(int p, int q, int id, int* task, int* succ, int cap);
+
+/*
  * blr_tc_gemm_selftest -- D = A B (device, column-major, FP64 in and out:
  * A m x k, lda >= m; B k x n, ldb >= k; D m x n, ldd >= m) through the
  * tensor-core building block of the mixed-precision updates (tcgen05 TF32

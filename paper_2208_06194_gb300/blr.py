@@ -84,6 +84,7 @@ _SIGS = {
     "blr_destroy_factor": (None, [_P]),
     "blr_dag_selfcheck": (_I, [_I, _I, ctypes.c_uint]),
     "blr_batch_selfcheck": (_I, [_IP, _IP, _I, ctypes.c_uint]),
+    "blr_dag_task": (_I, [_I, _I, _I, _IP, _IP, _I]),
     "blr_tc_gemm_selftest": (_I, [_P, _I, _P, _I, _P, _I, _I, _I, _I, _P]),
 }
 EXPORTED = tuple(_SIGS)
@@ -399,6 +400,16 @@ def blr_batch_selfcheck(ps, qs, seed: int = 0) -> int:
     p = np.ascontiguousarray(ps, dtype=np.int32)
     q = np.ascontiguousarray(qs, dtype=np.int32)
     return lib().blr_batch_selfcheck(p.ctypes.data_as(_IP), q.ctypes.data_as(_IP), len(p), seed)
+
+
+def blr_dag_task(p: int, q: int, task_id: int) -> tuple[tuple[int, int, int, int], list[int]]:
+    """(type, i, j, k) of a scheduler task id and the ids it releases (host only)."""
+    task = (ctypes.c_int * 4)()
+    succ = (ctypes.c_int * (q + 1))()
+    n = lib().blr_dag_task(p, q, task_id, task, succ, q + 1)
+    if n < 0:
+        raise BLRError(1, blr_last_error())
+    return tuple(task), list(succ[:n])
 
 
 def blr_dag_selfcheck(p: int, q: int, seed: int = 0) -> int:

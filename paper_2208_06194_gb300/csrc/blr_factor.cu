@@ -418,6 +418,29 @@ extern "C" int blr_batch_selfcheck(const int* p, const int* q, int count, unsign
 // exactly once, after all of its predecessors, and that the per-tile writer
 // chains of Algorithm 4 are respected.  Returns 0 on success, or a positive
 // code naming the first failed check.
+extern "C" int blr_dag_task(int p, int q, int id, int* task, int* succ, int cap) {
+  if (p < 1 || q < 1 || q > p || !task || !succ || cap < q + 1) {
+    blr_set_error("blr_dag_task: bad shape (p=%d, q=%d), NULL pointer or cap=%d < q+1", p, q, cap);
+    return -1;
+  }
+  std::vector<int> offL(q + 1), offS(q + 1), offP(q + 1);
+  const int n = dag_offsets(p, q, offL.data(), offS.data(), offP.data());
+  if (id < 0 || id >= n) {
+    blr_set_error("blr_dag_task: id %d outside [0, %d)", id, n);
+    return -1;
+  }
+  DagShape d{p, q, offL.data(), offS.data(), offP.data()};
+  int i, j, k;
+  const int t = dag_decode(d, id, &i, &j, &k);
+  task[0] = t; task[1] = i; task[2] = j; task[3] = k;
+  int ns = 0;
+  dag_for_each_successor(d, t, i, j, k, [&](int sid) {
+    if (ns < cap) succ[ns] = sid;
+    ns++;
+  });
+  return ns;
+}
+
 extern "C" int blr_dag_selfcheck(int p, int q, unsigned seed) {
   if (p < 1 || q < 1 || q > p) return 100;
   std::vector<int> offL(q + 1), offS(q + 1), offP(q + 1);
