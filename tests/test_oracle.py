@@ -221,6 +221,25 @@ def test_compress_qrcp_tolerance_and_exact_rank():
         assert np.linalg.norm(t.dense() - tile) <= eps * np.linalg.norm(tile)
         s = np.linalg.svd(tile, compute_uv=False)
         assert t.kind == "D" or t.rank >= O.truncation_rank(s, eps)
+    # pivots take the largest remaining column: on the smooth tile the rank
+    # stays within a few of the SVD's optimum (a pivot on a small column
+    # inflates it past the dense threshold)
+    t = O.compress_qrcp(tile, 1e-4, 32)
+    s = np.linalg.svd(tile, compute_uv=False)
+    assert t.kind == "L" and t.rank <= O.truncation_rank(s, 1e-4) + 4
+    # orthogonal columns of norms 10^-l in shuffled positions among zero
+    # columns: the pivoted QR takes them largest first, so its truncation is
+    # the SVD's exactly (same rank, same leading directions)
+    sig = 10.0 ** -np.arange(12.0)
+    uo, _ = np.linalg.qr(rng.standard_normal((b, 12)))
+    cols = rng.permutation(b)[:12]
+    a = np.zeros((b, b))
+    a[:, cols] = uo * sig
+    for eps in [1e-3, 1e-7, 1e-11]:
+        t = O.compress_qrcp(a, eps, b // 2)
+        r = O.truncation_rank(sig, eps)
+        assert t.kind == "L" and t.rank == r
+        assert np.allclose(np.abs(t.u), np.abs(uo[:, :r]), atol=1e-12)
     # full-rank random tile needs rank > b/2 -> dense, unchanged
     g = rng.standard_normal((b, b))
     t = O.compress_qrcp(g, 1e-8, b // 2)
@@ -268,6 +287,29 @@ def test_apply_q_roundtrip_and_qt_a_is_r():
     qta = O.apply_qt(f, a)
     assert np.allclose(qta[:48], f.r_dense(), atol=1e-12 * np.abs(a).max())
     assert np.abs(qta[48:]).max() < 1e-12 * np.abs(a).max()
+
+
+def test_metrics_measure_planted_errors():
+    """Res and Orth (Section 5) on errors of known size: against (1 + d) A an
+    exact factorization has Res = d / (1 + d); a Q whose every column is
+    scaled by (1 + d) (the thin Q of the exact factor times (1 + d)) has
+    Q^T Q - I = ((1 + d)^2 - 1) I, so Orth = (2d + d^2) sqrt(n) / sqrt(n)."""
+    a = W.random_blr_dense(96, 48, 8, 2, seed=3)
+    blr = O.compress(tiles_of(a, 8), 12, 6, 8, eps=1e-14)
+    f = O.blr_qr(blr, 1e-15)
+    for d in (1e-3, 1e-6):
+        assert O.residual(f, a * (1 + d)) == pytest.approx(d / (1 + d), rel=1e-6)
+    q1 = O.thin_q(f)
+    assert q1.shape == (96, 48)
+    for d in (1e-3, 1e-6):
+        scaled = q1 * (1 + d)
+        orth = np.linalg.norm(scaled.T @ scaled - np.eye(48)) / math.sqrt(48)
+        assert orth == pytest.approx(2 * d + d * d, rel=1e-6)
+    assert O.orthogonality(f) < 1e-13
+    # thin_q is Q [I; 0]: Q^T applied to it gives back [I; 0]
+    e = np.zeros((96, 48))
+    e[:48] = np.eye(48)
+    assert np.allclose(O.apply_qt(f, q1), e, atol=1e-13)
 
 
 def test_lstsq_matches_library_and_refinement():
