@@ -384,10 +384,43 @@ def test_rcb_order_leaves_and_boxes():
         assert (np.diff(ids) > 0).all()
 
 
+@pytest.mark.parametrize("seed", [0, 1, 2, 3])
+def test_rcb_odd_leaf_count_and_anisotropic_box(seed):
+    """5 leaves: the first split sends ceil(5/2) = 3 leaves left, along the
+    box's longest side (x: extents 3, 2, 0.25); the left 3 leaves then split
+    2 + 1 along their own longest side (y for most draws)."""
+    pts = np.random.default_rng(seed).random((3, 5 * 4)) * np.array([[3.0], [2.0], [0.25]])
+    perm = W.rcb_order(pts, 4)
+    assert sorted(perm.tolist()) == list(range(20))
+    assert pts[0, perm[:12]].max() <= pts[0, perm[12:]].min()
+    sub = pts[:, perm[:12]]
+    d2 = int(np.argmax(sub.max(1) - sub.min(1)))
+    assert pts[d2, perm[:8]].max() <= pts[d2, perm[8:12]].min()
+
+
 def test_ill_conditioned_scale():
     d = W.ill_conditioned_scale(11)
     assert d[0] == 1.0 and np.isclose(d[-1], 1e-10)
     assert np.allclose(d[1:] / d[:-1], 10 ** (-1.0))
+
+
+def test_column_scaling_is_a_right_diagonal_factor():
+    """The ill-conditioned variant is A D with D = diag(d) acting on columns:
+    every block is the unscaled block times d of its columns, and the dense
+    QR of A D has R(A D) = R(A) D up to row signs (Householder QR commutes
+    with a positive column scaling in exact arithmetic)."""
+    base = W.kernel_problem("yukawa3d", 48, 24, 8, 31, 32)
+    ill = W.kernel_problem("yukawa3d", 48, 24, 8, 31, 32, ill_conditioned=True)
+    d = W.ill_conditioned_scale(24)
+    assert np.allclose(ill.block(8, 24, 0, 8), base.block(8, 24, 0, 8) * d[None, :8], rtol=1e-15)
+    assert np.allclose(ill.block(0, 24, 0, 24), base.block(0, 24, 0, 24) * d[None, :], rtol=1e-15)
+    a, ad = base.dense(), ill.dense()
+    r_a = D.sign_normalize(np.linalg.qr(a, mode="r"))
+    r_ad = D.sign_normalize(np.linalg.qr(ad, mode="r"))
+    # column j of R(A) D: compare column by column relative to its own size
+    want = r_a * d[None, :]
+    for j in range(24):
+        assert np.linalg.norm(r_ad[:, j] - want[:, j]) <= 1e-8 * np.linalg.norm(want[:, j])
 
 
 # ---------------------------------------------------------------- blocked variant (Section 3.3)

@@ -1,9 +1,9 @@
 """Planted mistakes in the oracle, on the CPU: each pin must catch them.
 
-A mutant is one oracle function recompiled from its own source with one
-plausible slip (a dropped term, a wrong sign, a transposed operand, an
-off-by-one, a wrong loop order) and patched into the oracle modules for the
-duration of one test.  The pins of tests/test_oracle.py named beside it must
+A mutant is one oracle (or input-generator) function recompiled from its
+own source with one plausible slip (a dropped term, a wrong sign, a
+transposed operand, an off-by-one, a wrong loop order) and patched into the
+modules that bind it for the duration of one test.  The pins of tests/test_oracle.py named beside it must
 then fail; without a mutant they pass (that file's own run).
 """
 import inspect
@@ -13,6 +13,7 @@ import pytest
 
 from oracle import blr_qr as O
 from oracle import dense_qr as D
+from paper_2208_06194_gb300 import workloads as W
 from tests import test_oracle as T
 
 
@@ -59,6 +60,11 @@ PINS = {
     "metrics": T.test_metrics_measure_planted_errors,
     "blocked_full_rank": lambda: T.test_blocked_full_rank_equals_dense_qr(32, 16, 4),
     "blocked_low_rank": lambda: T.test_blocked_exact_low_rank_matches_dense_and_tiled(96, 48, 8, 1),
+    "kernels": T.test_kernel_entries_closed_form,
+    "rcb": T.test_rcb_order_leaves_and_boxes,
+    "rcb_odd": lambda: [T.test_rcb_odd_leaf_count_and_anisotropic_box(s) for s in range(4)],
+    "scale": T.test_ill_conditioned_scale,
+    "column_scaling": T.test_column_scaling_is_a_right_diagonal_factor,
 }
 
 # (what the slip is, function, source text, replacement, pins that must fail)
@@ -124,13 +130,29 @@ MUTANTS = [
      "left_dense(t.T, s)", "left_dense(t, s)", ["blocked_full_rank", "blocked_low_rank"]),
     ("apply_block_column_reflector: one row of the sum dropped", "apply_block_column_reflector",
      "s = x if s is None else add(s, x, eps, cap)", "s = x", ["blocked_full_rank", "blocked_low_rank"]),
+    # the seeded generators both sides take their inputs from
+    ("kernel_entries: squared distance", "kernel_entries", "r = np.sqrt(diff2)", "r = diff2", ["kernels"]),
+    ("kernel_entries: exp(+r)", "kernel_entries", "np.exp(-r)", "np.exp(r)", ["kernels"]),
+    ("kernel_entries: rows scaled instead of columns", "kernel_entries",
+     "a * col_scale[None, :]", "a * col_scale[:a.shape[0], None]", ["column_scaling"]),
+    ("rcb_order: split along the shortest side", "rcb_order",
+     "dim = int(np.argmax(ext))", "dim = int(np.argmin(ext))", ["rcb", "rcb_odd"]),
+    ("rcb_order: floor(L/2) leaves to the left", "rcb_order",
+     "int(math.ceil(leaves / 2)) * b", "(leaves // 2) * b", ["rcb_odd"]),
+    ("rcb_order: leaf points not in original order", "rcb_order",
+     "out.append(np.sort(ids))", "out.append(ids)", ["rcb"]),
+    ("ill_conditioned_scale: divides by n", "ill_conditioned_scale",
+     "np.arange(n) / (n - 1)", "np.arange(n) / n", ["scale"]),
+    ("random_blr_dense: full-rank off-diagonal tiles", "random_blr_dense",
+     "t = rng.standard_normal((b, k)) @ rng.standard_normal((b, k)).T", "t = rng.standard_normal((b, b))",
+     ["low_rank"]),
 ]
 
 
 def plant(monkeypatch, name, old, new):
     """Recompile oracle function `name` with `old` replaced by `new` and
     patch it into every oracle module that binds it."""
-    mods = [m for m in (O, D) if name in vars(m)]
+    mods = [m for m in (O, D, W) if name in vars(m)]
     original = getattr(mods[0], name)
     src = textwrap.dedent(inspect.getsource(original))
     assert src.count(old) == 1, f"{name}: planted text must occur exactly once"
