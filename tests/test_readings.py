@@ -112,3 +112,40 @@ def test_whole_block_t_from_inner_blocks_and_gram(b, nb):
         v = full[:, j]
         q = q @ (np.eye(2 * b) - tau[j] * np.outer(v, v))
     assert np.allclose(np.eye(2 * b) - full @ t @ full.T, q, atol=1e-12)
+
+
+# ---------------------------------------------------------------- reading 9
+
+def _rounded_addition_qrcp(ua, va, ub, vb, eps):
+    """Reading 9: Algorithm 6 with the s x s core R_U R_V^T truncated by a
+    column-pivoted QR (stop at the first r whose trailing block has Frobenius
+    norm <= eps times the core's) instead of its SVD."""
+    qu, ru = np.linalg.qr(np.hstack([ua, ub]))
+    qv, rv = np.linalg.qr(np.hstack([va, vb]))
+    c = ru @ rv.T
+    t = O.compress_qrcp(c, eps, c.shape[1])     # C ~ Q_C R_C P^T: U = Q_C, V = P R_C^T
+    if t.kind == "D":
+        return qu @ c @ qv.T, c.shape[1]
+    return qu @ t.u @ (qv @ t.v).T, t.rank
+
+
+@pytest.mark.parametrize("decay", [0.5, 0.1])
+def test_pivoted_qr_core_truncation_meets_the_bound(decay):
+    """The pivoted-QR truncation of the core meets Algorithm 6's Frobenius
+    bound (||C - C_r||_F <= eps ||C||_F, exact because Q_U and Q_V are
+    orthonormal) with a rank at or a few above the SVD's."""
+    rng = np.random.default_rng(int(decay * 10))
+    b, ra, rb = 64, 10, 12
+    sig = decay ** np.arange(ra + rb)
+    x, _ = np.linalg.qr(rng.standard_normal((b, ra + rb)))
+    z, _ = np.linalg.qr(rng.standard_normal((b, ra + rb)))
+    total = x @ np.diag(sig) @ z.T                    # A + B with a known spectrum
+    ua, _ = np.linalg.qr(rng.standard_normal((b, ra)))
+    va = rng.standard_normal((b, ra))
+    ub = np.hstack([x, ua])                             # B = total - A as a rank-(ra+rb+ra) product
+    vb = np.hstack([z * sig, -va])
+    for eps in (1e-2, 1e-5, 1e-9):
+        got, r = _rounded_addition_qrcp(ua, va, ub, vb, eps)
+        assert np.linalg.norm(got - total) <= eps * np.linalg.norm(total) * (1 + 1e-8) + 1e-14
+        r_svd = O.truncation_rank(sig, eps)
+        assert r_svd <= r <= r_svd + 3, (eps, r, r_svd)
