@@ -112,6 +112,13 @@ def test_whole_block_t_from_inner_blocks_and_gram(b, nb):
         v = full[:, j]
         q = q @ (np.eye(2 * b) - tau[j] * np.outer(v, v))
     assert np.allclose(np.eye(2 * b) - full @ t @ full.T, q, atol=1e-12)
+    # reading 7: applying the inner blocks one after another (the stored
+    # T_J, nb reflectors each) is the same Q
+    q_inner = np.eye(2 * b)
+    for j0 in range(0, b, nb):
+        vj = full[:, j0:j0 + nb]
+        q_inner = q_inner @ (np.eye(2 * b) - vj @ t[j0:j0 + nb, j0:j0 + nb] @ vj.T)
+    assert np.allclose(q_inner, q, atol=1e-12)
 
 
 # ---------------------------------------------------------------- reading 9
