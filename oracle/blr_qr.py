@@ -34,7 +34,10 @@ a rank-0 tile is a valid low-rank tile with empty factors.
 Pins: see tests/test_oracle.py.  The whole factorization is pinned to the
 textbook dense QR (oracle/dense_qr.py) in the full-rank case; the tile
 kernels to explicit dense reflector products; Algorithm 6 to its error bound
-and orthonormality; compression to its defining tolerance.
+and orthonormality; compression to its defining tolerance and to
+largest-norm pivoting; Res and Orth to closed forms on planted errors.
+tests/test_oracle_mutations.py plants one-slip mistakes in these functions
+and checks that the pins catch each of them.
 """
 from __future__ import annotations
 
