@@ -217,6 +217,14 @@ def probes(blr, fac, a_clone, pr, torch, dev, k=16, seed=5):
 _SAMPLE = {}
 
 
+def dense_equivalent(m: int, n: int, seconds: float) -> dict:
+    """Context only: the rate a dense Householder QR of the same m x n
+    matrix would need to finish in `seconds` ((2 m n^2 - 2 n^3 / 3) flop)."""
+    flop = 2.0 * m * n * n - 2.0 * n ** 3 / 3.0
+    return {"tflops": flop / seconds / 1e12, "flop": flop,
+            "note": "context only: (2mn^2 - 2n^3/3) / time, the work of a dense Householder QR"}
+
+
 def tpmqrt_kinds(st):
     """Trapezoidal updates by operand kinds (D dense, L low-rank) of Y~_ik,
     R_kj and A_ij: count, summed CTA-seconds, counted GFLOP."""
@@ -539,6 +547,7 @@ def main():
         "kernel_seconds": k_sec,
         "task_cta_seconds": dict(zip(["geqrt", "larfb", "tsqrt", "tpmqrt"], st["task_seconds"])),
         "tpmqrt_kinds": tpmqrt_kinds(st),
+        "dense_equivalent": dense_equivalent(s["m"], s["n"], t_step),
         "roofline": roofline(st, k_sec, prec == blr.BLR_PREC_FP64),
         "clocks": clk,
         "gpu_launches": args.steps,

@@ -77,3 +77,13 @@ def test_workload_name_names_sizes_and_variant():
     assert "65536x32768" in name and "b=512" in name and "tol=1e-05" in name
     args.ill_conditioned = True
     assert bench.workload_name(args).endswith("columns scaled 1..1e-10")
+
+
+def test_dense_equivalent_rate():
+    m, n = 65536, 32768
+    d = bench.dense_equivalent(m, n, 3.5)
+    assert d["flop"] == pytest.approx(2 * m * n * n - 2 * n ** 3 / 3)
+    assert d["tflops"] == pytest.approx(d["flop"] / 3.5 / 1e12)
+    assert d["note"].startswith("context only")
+    # square case: 4/3 n^3
+    assert bench.dense_equivalent(3, 3, 1.0)["flop"] == pytest.approx(4 / 3 * 27)
