@@ -52,8 +52,10 @@ typedef struct blr_batch_plan blr_batch_plan; /* opaque launch plan for one or s
 /*
  * Options.  Zero-initialise, then set what you need (blr_opts_default fills
  * the defaults).
- *  b            tile size; a multiple of 32 in [32, 1024]; m and n must be
- *               multiples of b (Section 2 tiling).
+ *  b            tile size; a multiple of 32 in [32, 512] (larger tiles are
+ *               rejected with BLR_ERR_INVALID: the shared-memory panel
+ *               buffer holds 513 x 32 doubles); m and n must be multiples
+ *               of b (Section 2 tiling).
  *  tol          compression tolerance: per tile, the smallest rank r with
  *               ||A_ij - U V^T||_F <= tol ||A_ij||_F (Section 3.1), found by
  *               truncated pivoted QR; ignored when fixed_rank > 0.

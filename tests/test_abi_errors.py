@@ -67,6 +67,7 @@ def _compress_kernel(L, x, y, dim, m, n, kid, o):
     ("n = 0", 128, 0, 1, 3, {"b": 128}, "multiples of b"),
     ("b not a multiple of 32", 96 * 4, 96 * 2, 1, 3, {"b": 96 + 8}, "multiple of 32"),
     ("b above the maximum", 8192, 4096, 1, 3, {"b": 4096}, "multiple of 32"),
+    ("b = 1024 (tiles above 512 not supported)", 2048, 1024, 1, 3, {"b": 1024}, "[32, 512]"),
     ("unknown kernel", 256, 128, 3, 3, {"b": 128}, "unknown kernel"),
     ("1D kernel with 3D points", 256, 128, 0, 3, {"b": 128}, "dim=1"),
     ("fixed rank above b/2", 256, 128, 1, 3, {"b": 128, "fixed_rank": 65}, "fixed_rank"),
