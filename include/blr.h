@@ -186,7 +186,8 @@ int blr_matrix_clone(const blr_matrix* a, blr_matrix** out, void* stream);
  *  a       consumed: its tiles become the factor's in-place storage and the
  *          handle is invalidated (do not use or destroy it afterwards; the
  *          factor owns the memory).  Clone it first to keep A~.
- *  opts    rec_tol, dense_rank, precision, sched_ctas, watchdog_ms are used.
+ *  opts    rec_tol (0: tol), dense_rank, precision, sched_ctas, watchdog_ms
+ *          and scratch_b2 are used; b comes from the matrix.
  *  f       receives the factor.  Tile (k,k) holds R_kk (upper) and Y_kk
  *          (strictly lower, unit diagonal implied); tile (k,j), j > k, holds
  *          R_kj; tile (i,k), i > k, holds Y~_ik = U_ik Y_ik (low-rank: U slot
