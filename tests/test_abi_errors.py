@@ -218,3 +218,13 @@ def test_python_binding_raises_without_a_device(L):
         blr.blr_compress_kernel(_points(256, 3).T, _points(128, 3).T, "yukawa3d", _opts(b=128, tol=1e-8),
                                 stream=0)
     assert e.value.code == CUDA
+
+
+def test_missing_library_fails_loudly(monkeypatch, tmp_path):
+    """No CPU fallback: without the built library every binding call raises."""
+    monkeypatch.setattr(blr, "_lib", None)
+    monkeypatch.setattr(blr, "LIB_PATH", str(tmp_path / "libblrqr.so"))
+    with pytest.raises(RuntimeError, match="is missing"):
+        blr.blr_opts_default()
+    with pytest.raises(RuntimeError, match="is missing"):
+        blr.blr_dag_selfcheck(2, 1)
