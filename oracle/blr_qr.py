@@ -12,7 +12,10 @@ Low-Rank Matrices"):
   U, V of b x r; U has orthonormal columns because compression is a
   truncated rank-revealing QR (Section 3.1 and Section 5).
 * Compression rank: smallest r with ||A_ij - U V^T||_F <= eps ||A_ij||_F
-  (Section 3.1); tiles needing rank > b/2 stay dense (Section 3.1).
+  (Section 3.1); tiles needing rank > b/2 stay dense (Section 3.1), or
+  above a lower dense threshold given with the matrix.
+* Strong admissibility (Section 3.1, eta): tiles whose row and column
+  clusters are near stay dense (strong_admissibility).
 * OP1..OP4 and the rounded addition of Algorithm 6 (Section 3.1).
 * Tiled Householder QR, Algorithm 4, with the BLR tile kernels of
   Section 3.4: diagonal QR (3.4.1), apply block reflector (3.4.2), update QR
@@ -28,7 +31,9 @@ Low-Rank Matrices"):
 Readings where the paper is silent (the same list is kept in the design
 notes): Householder sign convention of LAPACK; Algorithm 6 truncates at the
 smallest r whose Frobenius tail is <= eps times the norm of the sum itself;
-a low-rank result whose rank exceeds b/2 is stored dense (the exact sum);
+a low-rank result whose rank exceeds the dense threshold (b/2 by default,
+the value the paper names, or a lower one given with the matrix) is stored
+dense (the exact sum);
 a rank-0 tile is a valid low-rank tile with empty factors.
 
 Pins: see tests/test_oracle.py.  The whole factorization is pinned to the
@@ -157,9 +162,15 @@ class BLRMatrix:
     q: int
     b: int
     tiles: list            # tiles[i][j]
+    dense_rank: int = 0    # dense threshold; 0 (or anything outside [1, b/2]) means b/2
 
     @property
     def cap(self) -> int:
+        """Largest rank a low-rank tile may have: a tile (or a rounded sum)
+        that needs more is stored dense (Section 3.1's fallback, applied
+        with the threshold b/2 the paper names, or a lower one)."""
+        if 0 < self.dense_rank <= self.b // 2:
+            return self.dense_rank
         return self.b // 2
 
     def dense(self) -> np.ndarray:
@@ -172,30 +183,63 @@ class BLRMatrix:
 
     def copy(self) -> "BLRMatrix":
         return BLRMatrix(self.p, self.q, self.b,
-                         [[t.copy() for t in row] for row in self.tiles])
+                         [[t.copy() for t in row] for row in self.tiles], self.dense_rank)
 
     def ranks(self) -> np.ndarray:
         return np.array([[t.rank for t in row] for row in self.tiles])
 
 
 def compress(tile_fn, p: int, q: int, b: int, eps: float = 0.0,
-             fixed_rank: int = 0) -> BLRMatrix:
-    """BLR matrix under weak admissibility: diagonal tiles dense, every
-    other tile compressed (fixed rank by truncated SVD, or tolerance eps by
-    truncated QRCP; rank > b/2 falls back to dense)."""
-    tiles = []
+             fixed_rank: int = 0, dense_rank: int = 0, inadmissible=None) -> BLRMatrix:
+    """BLR matrix: diagonal tiles dense (weak admissibility), and so is every
+    tile (i,j) with inadmissible[i][j] true (strong admissibility, see
+    strong_admissibility); every other tile compressed (fixed rank by
+    truncated SVD, or tolerance eps by truncated QRCP; a tile that needs a
+    rank above the dense threshold -- dense_rank, or b/2 when 0 -- falls back
+    to dense)."""
+    out = BLRMatrix(p, q, b, [], dense_rank)
     for i in range(p):
         row = []
         for j in range(q):
             a = tile_fn(i, j)
-            if i == j:
+            if i == j or (inadmissible is not None and inadmissible[i][j]):
                 row.append(dense_tile(a))
             elif fixed_rank > 0:
                 row.append(compress_svd(a, fixed_rank))
             else:
-                row.append(compress_qrcp(a, eps, b // 2))
-        tiles.append(row)
-    return BLRMatrix(p, q, b, tiles)
+                row.append(compress_qrcp(a, eps, out.cap))
+        out.tiles.append(row)
+    return out
+
+
+def strong_admissibility(x: np.ndarray, y: np.ndarray, b: int, eta: float) -> np.ndarray:
+    """Inadmissible (near) tiles under strong admissibility (Section 3.1,
+    eta): the row cluster i is the points x[:, i b:(i+1) b], the column
+    cluster j the points y[:, j b:(j+1) b]; tile (i,j) is near, and stays
+    dense, when the distance between the two clusters' axis-aligned
+    bounding boxes is below eta times the larger of the two box diameters.
+    The paper names eta and says that a larger eta leaves more blocks
+    inadmissible without printing a formula; this is the standard box
+    criterion with that property.  Returns a p x q boolean array."""
+    x = np.asarray(x, dtype=np.float64)
+    y = np.asarray(y, dtype=np.float64)
+    p, q = x.shape[1] // b, y.shape[1] // b
+
+    def boxes(pts, n):
+        return [(pts[:, c * b:(c + 1) * b].min(axis=1), pts[:, c * b:(c + 1) * b].max(axis=1))
+                for c in range(n)]
+
+    bx, by = boxes(x, p), boxes(y, q)
+    near = np.zeros((p, q), dtype=bool)
+    for i in range(p):
+        ilo, ihi = bx[i]
+        for j in range(q):
+            jlo, jhi = by[j]
+            gap = np.maximum(0.0, np.maximum(jlo - ihi, ilo - jhi))
+            dist = math.sqrt(float(np.sum(gap * gap)))
+            diam = max(math.sqrt(float(np.sum((ihi - ilo) ** 2))), math.sqrt(float(np.sum((jhi - jlo) ** 2))))
+            near[i, j] = dist < eta * diam
+    return near
 
 
 # ----------------------------------------------------------------------------

@@ -194,6 +194,94 @@ def test_rounded_addition_over_cap_goes_dense():
     assert np.allclose(out.d, ua @ va.T + ub @ vb.T, atol=1e-13)
 
 
+def test_dense_threshold_below_half_b():
+    """A dense threshold below b/2 (Section 3.1's dense fallback with a lower
+    threshold): a sum or a tile whose rank exceeds it is stored dense (the
+    exact sum / the tile itself), one at the threshold stays low-rank; the
+    factorization keeps every low-rank tile at or below the threshold and
+    still equals the textbook dense QR (QR uniqueness)."""
+    rng = np.random.default_rng(17)
+    b = 16
+    uo, _ = np.linalg.qr(rng.standard_normal((b, 5)))
+    vo = rng.standard_normal((b, 5))
+    c = uo @ vo.T                                  # exact rank 5
+    for cap, kind in [(4, "D"), (5, "L"), (8, "L")]:
+        out = O.rounded_addition(uo[:, :3], vo[:, :3], uo[:, 3:], vo[:, 3:], 1e-12, cap)
+        assert out.kind == kind, cap
+        assert np.linalg.norm(out.dense() - c) <= 1e-12 * np.linalg.norm(c)
+        if kind == "L":
+            assert out.rank == 5
+        t = O.compress_qrcp(c, 1e-12, cap)
+        assert t.kind == kind, cap
+        if kind == "D":
+            assert np.array_equal(t.d, c)
+        else:
+            assert t.rank == 5
+    # the matrix carries its threshold; 0 and values above b/2 mean b/2
+    assert O.BLRMatrix(1, 1, 16, [], 3).cap == 3
+    assert O.BLRMatrix(1, 1, 16, [], 0).cap == 8
+    assert O.BLRMatrix(1, 1, 16, [], 9).cap == 8
+    # compression at threshold 2 of exact ranks 1..3: rank-3 tiles dense
+    m, n, b = 96, 48, 8
+    a = np.zeros((m, n))
+    ranks = {}
+    for j in range(n // b):
+        for i in range(m // b):
+            k = b if i == j else 1 + (i + 2 * j) % 3
+            a[i * b:(i + 1) * b, j * b:(j + 1) * b] = rng.standard_normal((b, k)) @ rng.standard_normal((k, b))
+            ranks[i, j] = k
+    blr = O.compress(tiles_of(a, b), m // b, n // b, b, eps=1e-14, dense_rank=2)
+    assert blr.cap == 2
+    for (i, j), k in ranks.items():
+        t = blr.tiles[i][j]
+        assert (t.kind == "D") == (i == j or k > 2), (i, j)
+        if t.kind == "L":
+            assert t.rank == k
+    f = O.blr_qr(blr, 1e-15)
+    rk = f.ranks()
+    assert rk.max() <= 2
+    assert (rk == -1).sum() > (blr.ranks() == -1).sum()       # sums above the threshold went dense
+    r_dense = np.linalg.qr(a, mode="r")
+    assert np.linalg.norm(D.sign_normalize(f.r_dense()) - D.sign_normalize(r_dense)) <= 1e-12 * np.linalg.norm(r_dense)
+    assert O.residual(f, a) < 1e-13
+
+
+def test_strong_admissibility_box_distance():
+    """Strong admissibility (Section 3.1, eta) on boxes computed by hand: a
+    tile is near when the gap between its clusters' bounding boxes is below
+    eta times the larger box diameter; a larger eta keeps more tiles dense;
+    eta = 0 keeps none."""
+    b = 2
+    # row clusters: box [0,1]^3 (diameter sqrt 3) and box [0,3] x [0,0] x [0,0] (diameter 3)
+    x = np.array([[0.0, 1.0, 0.0, 3.0],
+                  [0.0, 1.0, 0.0, 0.0],
+                  [0.0, 1.0, 0.0, 0.0]])
+    # column cluster: box [2,2.5] x [0,0] x [0,0] (diameter 0.5)
+    y = np.array([[2.0, 2.5],
+                  [0.0, 0.0],
+                  [0.0, 0.0]])
+    # gaps: cluster 0 -> (1, 0, 0): distance 1, larger diameter sqrt 3;
+    #       cluster 1 -> overlapping boxes: distance 0, larger diameter 3
+    for eta, want in [(0.0, [False, False]), (0.5, [False, True]), (1.0 / math.sqrt(3) - 1e-9, [False, True]),
+                      (1.0 / math.sqrt(3) + 1e-9, [True, True]), (2.0, [True, True])]:
+        near = O.strong_admissibility(x, y, b, eta)
+        assert near.shape == (2, 1)
+        assert list(near[:, 0]) == want, eta
+    # monotone in eta on a kernel workload; diagonal-distance ordering kept
+    pr = W.kernel_problem("yukawa3d", 1024, 512, 64, 5, 6)
+    counts = [int(O.strong_admissibility(pr.x, pr.y, 64, eta).sum()) for eta in (0.0, 0.3, 1.0, 3.0)]
+    assert counts[0] == 0 and counts == sorted(counts) and counts[-1] > counts[1]
+    # compress() keeps the near tiles dense, compresses the rest
+    near = O.strong_admissibility(pr.x, pr.y, 64, 1.0)
+    blr = O.compress(pr.tile, 16, 8, 64, eps=1e-3, inadmissible=near)
+    rk = blr.ranks()
+    assert (rk[near] == -1).all()
+    weak = O.compress(pr.tile, 16, 8, 64, eps=1e-3).ranks()
+    far = ~near & ~np.eye(16, 8, dtype=bool)
+    assert np.array_equal(rk[far], weak[far])
+    assert (weak[near & ~np.eye(16, 8, dtype=bool)] >= 0).any()    # near tiles that weak admissibility compresses
+
+
 def test_op3_op4_products():
     rng = np.random.default_rng(8)
     x = O.lr_tile(rng.standard_normal((7, 2)), rng.standard_normal((7, 2)))

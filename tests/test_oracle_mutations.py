@@ -65,6 +65,8 @@ PINS = {
     "rcb_odd": lambda: [T.test_rcb_odd_leaf_count_and_anisotropic_box(s) for s in range(4)],
     "scale": T.test_ill_conditioned_scale,
     "column_scaling": T.test_column_scaling_is_a_right_diagonal_factor,
+    "dense_threshold": T.test_dense_threshold_below_half_b,
+    "admissibility": T.test_strong_admissibility_box_distance,
 }
 
 # (what the slip is, function, source text, replacement, pins that must fail)
@@ -130,6 +132,19 @@ MUTANTS = [
      "left_dense(t.T, s)", "left_dense(t, s)", ["blocked_full_rank", "blocked_low_rank"]),
     ("apply_block_column_reflector: one row of the sum dropped", "apply_block_column_reflector",
      "s = x if s is None else add(s, x, eps, cap)", "s = x", ["blocked_full_rank", "blocked_low_rank"]),
+    ("compress: dense threshold ignored", "compress",
+     "compress_qrcp(a, eps, out.cap)", "compress_qrcp(a, eps, b // 2)", ["dense_threshold"]),
+    ("blr_qr: factorization ignores the dense threshold", "blr_qr",
+     "p, q, b, cap = a.p, a.q, a.b, a.cap", "p, q, b, cap = a.p, a.q, a.b, a.b // 2", ["dense_threshold"]),
+    ("compress: near tiles compressed", "compress",
+     "if i == j or (inadmissible is not None and inadmissible[i][j]):", "if i == j:", ["admissibility"]),
+    ("strong_admissibility: smaller diameter", "strong_admissibility",
+     "diam = max(math.sqrt", "diam = min(math.sqrt", ["admissibility"]),
+    ("strong_admissibility: gap from the box centres", "strong_admissibility",
+     "gap = np.maximum(0.0, np.maximum(jlo - ihi, ilo - jhi))",
+     "gap = np.abs((jlo + jhi) / 2 - (ilo + ihi) / 2)", ["admissibility"]),
+    ("strong_admissibility: rows and columns swapped", "strong_admissibility",
+     "bx, by = boxes(x, p), boxes(y, q)", "bx, by = boxes(x, q), boxes(y, p)", ["admissibility"]),
     # the seeded generators both sides take their inputs from
     ("kernel_entries: squared distance", "kernel_entries", "r = np.sqrt(diff2)", "r = diff2", ["kernels"]),
     ("kernel_entries: exp(+r)", "kernel_entries", "np.exp(-r)", "np.exp(r)", ["kernels"]),
