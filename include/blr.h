@@ -79,6 +79,15 @@ typedef struct blr_batch_plan blr_batch_plan; /* opaque launch plan for one or s
  *               0 = 20 (ample for every rank up to b/2).  A task that needs
  *               more fails the call with BLR_ERR_RANK_OVERFLOW (blr_stats
  *               reports the largest use, scratch_peak_bytes).
+ *  trace        blr_qr / blr_qr_batched: > 0 records one blr_trace_event per
+ *               task (type, tiles, CTA, SM, start and end time), keeping the
+ *               first `trace` of them (blr_trace_export); 0 = no trace.
+ *  test_withhold  test hook, 0 = off: 1 + the id of one task (numbered as
+ *               blr_dag_task numbers them; in a batch, ids of matrix t start
+ *               after all tasks of matrices 0..t-1) whose successors are
+ *               never released, so the scheduler stalls and the watchdog
+ *               ends the call with BLR_ERR_TIMEOUT.  Only a device wait that
+ *               runs out: nothing faults.
  */
 typedef struct blr_opts {
   int b;
@@ -90,10 +99,23 @@ typedef struct blr_opts {
   int sched_ctas;
   int watchdog_ms;
   int scratch_b2;
-  int reserved0;
+  int trace;
   double eta;
-  int reserved[4];
+  int test_withhold;
+  int reserved[3];
 } blr_opts;
+
+/* One task of a traced factorization (blr_trace_export). */
+typedef struct blr_trace_event {
+  int type;                 /* 0 GEQRT, 1 LARFB, 2 TSQRT, 3 TPMQRT */
+  int i, j, k;              /* its 0-based tile indices (as blr_dag_task gives them) */
+  int matrix;               /* matrix of a batched launch (0 for blr_qr) */
+  int cta;                  /* scheduler CTA that ran it */
+  int sm;                   /* SM that CTA ran on */
+  int reserved;
+  long long t_start_ns;     /* device global timer at the task's start */
+  long long t_end_ns;       /* ... at its end, before it released its successors */
+} blr_trace_event;
 
 /* Statistics of a handle (host struct filled by blr_stats). */
 typedef struct blr_stats_t {
@@ -253,10 +275,10 @@ int blr_apply_qt(const blr_factor* f, double* b_dev, int ldb, int nrhs, int tran
 
 /*
  * blr_apply_qt_noalloc -- the same operation as blr_apply_qt, for callers
- * that cannot allocate device memory during the call (inside a stream
- * capture that must stay allocation-free, under an application-owned pool
- * that forbids cudaMalloc after start-up, or where the allocator's implicit
- * synchronisation is unaffordable).  The paper has no counterpart: this is
+ * that cannot allocate device memory during the call (an application that
+ * owns all device memory through its own pool and forbids cudaMalloc after
+ * start-up, or a latency-critical solver that cannot afford the allocator's
+ * implicit device synchronisation).  The paper has no counterpart: this is
  * an interface variant of the Algorithm 5 apply.  Nothing is allocated: the
  * scratch is a 4 MiB static device array inside the library, held by every
  * GPU that loads it until the process exits.  Limit: the scratch must hold
@@ -332,6 +354,34 @@ int blr_factor_export_t(const blr_factor* f, double* t_host, void* stream);
 
 /* Statistics of a matrix or factor handle. */
 int blr_stats(const void* handle, int handle_is_factor, blr_stats_t* out);
+
+/*
+ * blr_trace_export -- the per-task trace of the launch that made f (opts.trace
+ * > 0; the execution traces of Section 5.1 for the device scheduler).  Copies
+ * min(cap, recorded) events into events_host (host, cap entries) in the order
+ * the tasks finished; *total (host, may be NULL) receives the number of tasks
+ * the launch ran (more than recorded when the trace capacity was smaller).
+ * A factor of a batched launch holds the whole batch's trace.  Returns the
+ * number copied, or -1 (BLR_ERR_INVALID, message in blr_last_error) for a
+ * NULL factor or events_host with cap > 0.
+ */
+int blr_trace_export(const blr_factor* f, blr_trace_event* events_host, int cap, long long* total);
+
+/*
+ * blr_densify -- a dense m x n (or n x n) column-major device array from BLR
+ * storage, for checks and for callers that need the explicit matrix
+ * (Eq. 7: a tile is its dense block or U V^T).
+ *  which = 0: every tile as stored (a matrix: A~; a factor: its in-place
+ *             storage, R above and reflector tails below the diagonal),
+ *             m x n;
+ *  which = 1: a factor's R (upper triangular, n x n);
+ *  which = 2: a factor's reflector tails Y~ (m x n: unit lower triangular
+ *             Y_kk on the diagonal tiles, Y~_ik = U_ik Y_ik below, zero above).
+ *  out_dev    device, ld >= m (which 0, 2) or >= n (which 1); the caller owns it.
+ * Errors: BLR_ERR_INVALID (NULL handle or out_dev, ld too small, which out
+ * of range, which 1 or 2 with a matrix handle), BLR_ERR_CUDA.
+ */
+int blr_densify(const void* handle, int handle_is_factor, int which, double* out_dev, int ld, void* stream);
 
 void blr_destroy_matrix(blr_matrix* a);
 void blr_destroy_factor(blr_factor* f);

@@ -33,8 +33,14 @@ class Opts(ctypes.Structure):
     _fields_ = [("b", ctypes.c_int), ("fixed_rank", ctypes.c_int), ("tol", ctypes.c_double),
                 ("rec_tol", ctypes.c_double), ("dense_rank", ctypes.c_int),
                 ("precision", ctypes.c_int), ("sched_ctas", ctypes.c_int),
-                ("watchdog_ms", ctypes.c_int), ("scratch_b2", ctypes.c_int), ("reserved0", ctypes.c_int),
-                ("eta", ctypes.c_double), ("reserved", ctypes.c_int * 4)]
+                ("watchdog_ms", ctypes.c_int), ("scratch_b2", ctypes.c_int), ("trace", ctypes.c_int),
+                ("eta", ctypes.c_double), ("test_withhold", ctypes.c_int), ("reserved", ctypes.c_int * 3)]
+
+
+class TraceEvent(ctypes.Structure):
+    _fields_ = [("type", ctypes.c_int), ("i", ctypes.c_int), ("j", ctypes.c_int), ("k", ctypes.c_int),
+                ("matrix", ctypes.c_int), ("cta", ctypes.c_int), ("sm", ctypes.c_int), ("reserved", ctypes.c_int),
+                ("t_start_ns", ctypes.c_longlong), ("t_end_ns", ctypes.c_longlong)]
 
 
 class Stats(ctypes.Structure):
@@ -80,6 +86,8 @@ _SIGS = {
     "blr_lstsq_backward": (_I, [_P, _P, _P, _I, _P, _I, _P, _I, _I, _P, _I, _P, _P]),
     "blr_factor_export_t": (_I, [_P, _DP, _P]),
     "blr_stats": (_I, [_P, _I, ctypes.POINTER(Stats)]),
+    "blr_trace_export": (_I, [_P, ctypes.POINTER(TraceEvent), _I, ctypes.POINTER(ctypes.c_longlong)]),
+    "blr_densify": (_I, [_P, _I, _I, _P, _I, _P]),
     "blr_destroy_matrix": (None, [_P]),
     "blr_destroy_factor": (None, [_P]),
     "blr_dag_selfcheck": (_I, [_I, _I, ctypes.c_uint]),
@@ -393,6 +401,49 @@ def blr_stats(obj) -> dict:
     for k in ("tpmqrt_kind", "tpmqrt_kind_seconds", "tpmqrt_kind_flops"):
         d[k] = list(getattr(s, k))
     return d
+
+
+TASK_NAMES = ("GEQRT", "LARFB", "TSQRT", "TPMQRT")
+
+
+def blr_trace_export(f: Factor) -> tuple[list[dict], int]:
+    """(events, tasks run) of a factorization made with opts.trace > 0; each
+    event a dict with the fields of blr_trace_event."""
+    total = ctypes.c_longlong(0)
+    n = lib().blr_trace_export(f.handle, None, 0, ctypes.byref(total))
+    if n < 0:
+        raise BLRError(1, blr_last_error())
+    cap = int(total.value)
+    buf = (TraceEvent * max(cap, 1))()
+    n = lib().blr_trace_export(f.handle, buf, cap, ctypes.byref(total))
+    if n < 0:
+        raise BLRError(1, blr_last_error())
+    return [{k: getattr(buf[e], k) for k, _ in TraceEvent._fields_ if k != "reserved"} for e in range(n)], \
+        int(total.value)
+
+
+def chrome_trace(events: list[dict]) -> dict:
+    """The task trace in the Chrome trace-event format (one row per
+    scheduler CTA, times in microseconds from the first task's start)."""
+    t0 = min((e["t_start_ns"] for e in events), default=0)
+    out = []
+    for e in events:
+        name = f"{TASK_NAMES[e['type']]}({e['i']},{e['j']},{e['k']})"
+        out.append({"name": name, "cat": TASK_NAMES[e["type"]], "ph": "X", "pid": e["matrix"], "tid": e["cta"],
+                    "ts": (e["t_start_ns"] - t0) / 1e3, "dur": (e["t_end_ns"] - e["t_start_ns"]) / 1e3,
+                    "args": {"sm": e["sm"]}})
+    return {"traceEvents": out, "displayTimeUnit": "ms"}
+
+
+def blr_densify(obj, which: int = 0, stream=None):
+    """Dense column-major CUDA tensor of a Matrix (which 0: A~) or of a
+    Factor (0: in-place storage, 1: R (n x n), 2: reflector tails Y~)."""
+    rows = obj.n if which == 1 else obj.m
+    cols = obj.n
+    out = fortran_empty(rows, cols)
+    _check(lib().blr_densify(obj.handle, 1 if isinstance(obj, Factor) else 0, which, ctypes.c_void_p(out.data_ptr()),
+                             rows, _stream(stream)))
+    return out
 
 
 def blr_batch_selfcheck(ps, qs, seed: int = 0) -> int:

@@ -4,6 +4,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <cmath>
+#include <algorithm>
 #include <vector>
 #include "blr_internal.h"
 
@@ -270,6 +271,10 @@ extern "C" int blr_matrix_clone(const blr_matrix* a, blr_matrix** out, void* str
 
 int blr_check_qr_opts(const blr_opts* opts) {
   if (!opts) { blr_set_error("opts is NULL"); return BLR_ERR_INVALID; }
+  if (opts->trace < 0 || opts->test_withhold < 0) {
+    blr_set_error("negative trace or test_withhold option");
+    return BLR_ERR_INVALID;
+  }
   if (opts->rec_tol < 0 || (opts->rec_tol == 0 && opts->tol <= 0)) {
     blr_set_error("blr_qr needs rec_tol > 0 or tol > 0");
     return BLR_ERR_INVALID;
@@ -283,8 +288,7 @@ int blr_check_qr_opts(const blr_opts* opts) {
 
 // A factor that takes over a's storage (a is deleted) and owns new T blocks.
 static int factor_adopt(blr_matrix* a, const blr_opts* opts, blr_factor** out) {
-  blr_factor* F = new blr_factor;
-  memset(F, 0, sizeof(*F));
+  blr_factor* F = new blr_factor();
   F->a = *a;
   delete a;   // the factor now owns the tiles
   F->opts = *opts;
@@ -386,6 +390,17 @@ extern "C" int blr_stats(const void* handle, int handle_is_factor, blr_stats_t* 
     }
   }
   return BLR_OK;
+}
+
+extern "C" int blr_trace_export(const blr_factor* f, blr_trace_event* events_host, int cap, long long* total) {
+  if (!f || (cap > 0 && !events_host) || cap < 0) {
+    blr_set_error("blr_trace_export: NULL factor, or NULL events with cap > 0");
+    return -1;
+  }
+  const int n = (int)std::min<size_t>((size_t)cap, f->trace.size());
+  if (n > 0) memcpy(events_host, f->trace.data(), sizeof(blr_trace_event) * (size_t)n);
+  if (total) *total = f->trace_total;
+  return n;
 }
 
 extern "C" void blr_destroy_matrix(blr_matrix* a) {

@@ -30,6 +30,7 @@ struct blr_batch_plan {
   int* seed = nullptr;                    // device: the count initially ready tasks, then count
   double* scratch = nullptr;
   float* prep = nullptr;
+  blr_trace_event* trace = nullptr;       // opts.trace events (device)
   SchedParams P{};
   int ctas = 0, n_tasks = 0;
   size_t slab = 0;
@@ -42,6 +43,7 @@ static void plan_free(blr_batch_plan* pl) {
   if (pl->e1) cudaEventDestroy(pl->e1);
   if (pl->scratch) cudaFree(pl->scratch);
   if (pl->prep) cudaFree(pl->prep);
+  if (pl->trace) cudaFree(pl->trace);
   if (pl->base) cudaFree(pl->base);
 #ifdef BLR_PHASE_TIMING
   if (pl->P.phase) cudaFree(pl->P.phase);
@@ -111,7 +113,7 @@ static int plan_build(blr_factor* const* fs, int count, const blr_opts* o, blr_b
                o_flops = take(sizeof(double) * 4), o_ntask = take(sizeof(unsigned long long) * 4),
                o_tns = take(sizeof(unsigned long long) * 4), o_nvar = take(sizeof(unsigned long long) * 8),
                o_tvar = take(sizeof(unsigned long long) * 8), o_fvar = take(sizeof(double) * 8),
-               o_peak = take(sizeof(unsigned long long));
+               o_peak = take(sizeof(unsigned long long)), o_tracen = take(sizeof(unsigned int));
   pl->dyn_bytes = bytes - pl->dyn_off;
   const int nsm = blr_num_sms();
   pl->ctas = o->sched_ctas > 0 ? o->sched_ctas : nsm;
@@ -134,8 +136,17 @@ static int plan_build(blr_factor* const* fs, int count, const blr_opts* o, blr_b
     pl->prep = nullptr;
     cudaGetLastError();
   }
+  if (o->trace > 0 && cudaMalloc(&pl->trace, sizeof(blr_trace_event) * (size_t)o->trace) != cudaSuccess) {
+    plan_free(pl);
+    blr_set_error("blr_qr: out of device memory (trace of %d events)", o->trace);
+    return BLR_ERR_OOM;
+  }
   char* base = pl->base;
   SchedParams& P = pl->P;
+  P.trace = pl->trace;
+  P.trace_cap = pl->trace ? o->trace : 0;
+  P.trace_n = (unsigned int*)(base + o_tracen);
+  P.withhold = o->test_withhold > 0 ? o->test_withhold - 1 : -1;
   P.precision = o->precision;
   P.rec_tol = o->rec_tol > 0 ? o->rec_tol : o->tol;
   P.n_tasks = total;
@@ -176,6 +187,7 @@ static int plan_build(blr_factor* const* fs, int count, const blr_opts* o, blr_b
     Q.prep = pl->prep ? pl->prep + M[m].prep_off : nullptr;
     Q.prep_rp = (A.b + 127) / 128 * 128;
     Q.task_base = M[m].base;
+    Q.mat_index = m;
     mbase[m] = M[m].base;
     seed[m] = M[m].base;   // GEQRT(0) of every matrix is ready at the start
     rc = blr_cuda_check(cudaMemcpy(base + M[m].o_offL, M[m].offL.data(), sizeof(int) * (M[m].q + 1), cudaMemcpyHostToDevice), "copy offsets");
@@ -260,10 +272,20 @@ static int plan_finish(blr_batch_plan* pl, cudaStream_t st) {
   cudaMemcpy(tv, P.tvar, sizeof(tv), cudaMemcpyDeviceToHost);
   cudaMemcpy(fv, P.fvar, sizeof(fv), cudaMemcpyDeviceToHost);
   cudaMemcpy(&peak, P.slab_peak, sizeof(peak), cudaMemcpyDeviceToHost);
+  unsigned int tn = 0;
+  std::vector<blr_trace_event> trace;
+  if (P.trace) {
+    cudaMemcpy(&tn, P.trace_n, sizeof(tn), cudaMemcpyDeviceToHost);
+    trace.resize(std::min<size_t>(tn, (size_t)P.trace_cap));
+    if (!trace.empty())
+      cudaMemcpy(trace.data(), P.trace, sizeof(blr_trace_event) * trace.size(), cudaMemcpyDeviceToHost);
+  }
   rc = blr_cuda_check(cudaGetLastError(), "read status");
   if (rc) return rc;
   // statistics of the whole launch (a batch reports the batch in every factor)
   for (blr_factor* f : pl->fac) {
+    f->trace = trace;
+    f->trace_total = tn;
     f->seconds = ms * 1e-3;
     f->scratch_peak_bytes = (long long)(peak * sizeof(double));
     f->scratch_bytes = (long long)(sizeof(double) * pl->slab * pl->ctas);

@@ -47,6 +47,10 @@ struct blr_matrix {
   size_t bytes;
 };
 
+#ifdef __cplusplus
+#include <vector>
+#endif
+
 struct blr_factor {
   blr_matrix a;    // in-place R / Y~ storage
   double* t;       // T blocks: for each (i,k), i >= k, 32 x b doubles
@@ -62,6 +66,8 @@ struct blr_factor {
   long long scratch_peak_bytes;
   long long scratch_bytes;
   double seconds;
+  std::vector<blr_trace_event> trace;   // host copy of the launch's task trace (opts.trace > 0)
+  long long trace_total;                // tasks the traced launch ran
 };
 
 // Parameters of the persistent scheduler kernel.
@@ -104,6 +110,12 @@ struct SchedParams {
   int nmat;                      // > 1: a batch (mats, mat_base valid)
   const SchedParams* mats;       // device, nmat entries
   const int* mat_base;           // device, nmat + 1 entries (task_base of each, then the total)
+  int mat_index;                 // this matrix's position in the batch
+  // task trace (opts.trace > 0): trace_cap events; trace_n counts the tasks
+  blr_trace_event* trace;
+  int trace_cap;
+  unsigned int* trace_n;
+  int withhold;                  // test hook: batch-wide id of a task that releases nothing, or -1
 };
 
 // host helpers (blr_api.cu)

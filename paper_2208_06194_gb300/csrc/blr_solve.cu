@@ -4,6 +4,7 @@
 // least squares, Section 1) and its adjoint.  Every kernel gives each CTA a
 // group of right-hand-side columns; the reflector sequence is applied in
 // order inside the CTA.
+#include <mutex>
 #include <cstdio>
 #include <vector>
 #include "blr_device.cuh"
@@ -338,15 +339,28 @@ int finish(const FactorView& F, cudaStream_t st, const char* what) {
   return BLR_OK;
 }
 
+// The dynamic shared-memory opt-in is a per-device attribute of each kernel:
+// set it once for every device that runs these kernels (with that device
+// current), under a lock.
+std::mutex g_smem_mu;
+bool g_smem_done[64];
+
 int set_smem() {
-  static bool done = false;
-  if (done) return BLR_OK;
-  int rc = blr_cuda_check(cudaFuncSetAttribute(k_apply_q, cudaFuncAttributeMaxDynamicSharedMemorySize, BLR_SMEM_BYTES), "smem");
+  int dev = 0;
+  int rc = blr_cuda_check(cudaGetDevice(&dev), "cudaGetDevice");
+  if (rc) return rc;
+  if (dev < 0 || dev >= 64) {
+    blr_set_error("device ordinal %d out of range", dev);
+    return BLR_ERR_INVALID;
+  }
+  std::lock_guard<std::mutex> lock(g_smem_mu);
+  if (g_smem_done[dev]) return BLR_OK;
+  rc = blr_cuda_check(cudaFuncSetAttribute(k_apply_q, cudaFuncAttributeMaxDynamicSharedMemorySize, BLR_SMEM_BYTES), "smem");
   if (!rc) rc = blr_cuda_check(cudaFuncSetAttribute(k_solve_r, cudaFuncAttributeMaxDynamicSharedMemorySize, BLR_SMEM_BYTES), "smem");
   if (!rc) rc = blr_cuda_check(cudaFuncSetAttribute(k_matmul, cudaFuncAttributeMaxDynamicSharedMemorySize, BLR_SMEM_BYTES), "smem");
   if (!rc) rc = blr_cuda_check(cudaFuncSetAttribute(k_solve_rt, cudaFuncAttributeMaxDynamicSharedMemorySize, BLR_SMEM_BYTES), "smem");
   if (!rc) rc = blr_cuda_check(cudaFuncSetAttribute(k_lstsq_grad, cudaFuncAttributeMaxDynamicSharedMemorySize, BLR_SMEM_BYTES), "smem");
-  if (!rc) done = true;
+  if (!rc) g_smem_done[dev] = true;
   return rc;
 }
 
@@ -554,11 +568,11 @@ extern "C" int blr_lstsq_backward(const blr_factor* f, const blr_matrix* a_orig,
 // ---------------------------------------------------------------------------
 // blr_apply_qt_noalloc: Q^T B / Q B without any device allocation.
 //
-// Some callers cannot allocate device memory at call time: code running
-// inside a stream capture that must not contain allocations, applications
-// with their own pool that forbids cudaMalloc after start-up, or latency-
-// critical solvers that cannot afford the allocator's implicit
-// synchronisation.  This entry point runs the same apply kernel as
+// Some callers cannot allocate device memory at call time: applications
+// that own all device memory through their own pool and forbid cudaMalloc
+// after start-up, and latency-critical solvers that cannot afford the
+// allocator's implicit device synchronisation in the middle of an
+// iteration.  This entry point runs the same apply kernel as
 // blr_apply_qt, with its scratch (status word, per-block-column T offsets,
 // per-CTA work slabs) in the fixed array below instead of cudaMalloc'd
 // buffers.  The array is a file-scope device variable, so every GPU that
@@ -567,9 +581,10 @@ extern "C" int blr_lstsq_backward(const blr_factor* f, const blr_matrix* a_orig,
 // clears the status word itself and every other byte it reads is written
 // first.  Calls whose kernels overlap on the GPU (different streams or
 // threads at the same time) race on this memory and must be serialised by
-// the caller.
+// the caller.  The first call on a device looks up the array's device
+// address with that device current (cudaGetSymbolAddress), so that first
+// call should come before any stream capture.
 // ---------------------------------------------------------------------------
-#include <mutex>
 
 #define BLR_NOALLOC_BYTES (4u << 20)
 static __device__ __align__(256) double g_apply_scratch[BLR_NOALLOC_BYTES / sizeof(double)];
@@ -655,4 +670,55 @@ extern "C" int blr_apply_qt_noalloc(const blr_factor* f, double* b_dev, int ldb,
     return BLR_ERR_NUMERIC;
   }
   return BLR_OK;
+}
+
+// ---------------------------------------------------------------------------
+// blr_densify: a dense column-major array from BLR storage (Eq. 7: a tile is
+// its dense block or U V^T).  One CTA per tile; consecutive threads take
+// consecutive rows of a column, so tile reads and output writes coalesce.
+// ---------------------------------------------------------------------------
+namespace {
+
+__global__ void __launch_bounds__(BLR_NT) k_densify(const double* tiles, const int* rank, int p, int q, int b,
+                                                    int cap, int which, double* out, long long ld) {
+  const int t = blockIdx.x;
+  const int i = t % p, j = t / p;
+  if (which == 1 && i >= q) return;                // R is n x n: tile rows below q are not part of it
+  const double* T = tiles + (size_t)t * b * b;
+  const int r = rank[t];
+  for (int e = threadIdx.x; e < b * b; e += blockDim.x) {
+    const int rr = e % b, cc = e / b;
+    double v;
+    if ((which == 1 && (j < i || (j == i && rr > cc))) || (which == 2 && j > i)) {
+      v = 0.0;                                     // below R's diagonal, or above Y~'s
+    } else if (which == 2 && i == j) {
+      v = rr > cc ? T[rr + (size_t)cc * b] : (rr == cc ? 1.0 : 0.0);   // unit lower triangular Y_kk
+    } else if (r < 0) {
+      v = T[rr + (size_t)cc * b];
+    } else {
+      double acc = 0.0;
+      for (int l = 0; l < r; l++) acc += T[rr + (size_t)l * b] * T[(size_t)b * cap + cc + (size_t)l * b];
+      v = acc;
+    }
+    out[(size_t)i * b + rr + (size_t)(j * b + cc) * ld] = v;
+  }
+}
+
+}  // namespace
+
+extern "C" int blr_densify(const void* handle, int handle_is_factor, int which, double* out_dev, int ld,
+                           void* stream) {
+  if (!handle || !out_dev) { blr_set_error("blr_densify: NULL handle or output"); return BLR_ERR_INVALID; }
+  if (which < 0 || which > 2 || (which > 0 && !handle_is_factor)) {
+    blr_set_error("blr_densify: which=%d is not valid for a %s handle", which, handle_is_factor ? "factor" : "matrix");
+    return BLR_ERR_INVALID;
+  }
+  const blr_matrix* a = handle_is_factor ? &((const blr_factor*)handle)->a : (const blr_matrix*)handle;
+  const int rows = which == 1 ? a->n : a->m;
+  if (ld < rows) { blr_set_error("blr_densify: ld=%d < %d rows", ld, rows); return BLR_ERR_INVALID; }
+  cudaStream_t st = (cudaStream_t)stream;
+  k_densify<<<a->p * a->q, BLR_NT, 0, st>>>(a->tiles, a->rank, a->p, a->q, a->b, a->cap, which, out_dev, ld);
+  int rc = blr_cuda_check(cudaGetLastError(), "launch k_densify");
+  if (!rc) rc = blr_cuda_check(cudaStreamSynchronize(st), "blr_densify");
+  return rc;
 }

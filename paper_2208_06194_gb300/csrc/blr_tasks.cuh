@@ -661,7 +661,7 @@ __device__ void task_tsqrt(TaskEnv& env, int i, int k, Ctx& c) {
       // then prepare the tensor-core operands for the updates TPMQRT(i,.,k)
       __threadfence();
       __syncthreads();
-      if (i + 1 < P.p && threadIdx.x == 0) {
+      if (i + 1 < P.p && threadIdx.x == 0 && P.task_base + dag_id_tsqrt(*env.dag, i, k) != P.withhold) {
         const int sid = dag_id_tsqrt(*env.dag, i + 1, k);
         release_task(P, *env.dag, sid);
         env.skip_succ = sid;
@@ -1167,6 +1167,7 @@ __global__ void __launch_bounds__(BLR_NT, 1) k_factor(SchedParams P) {
   __shared__ uint32_t tc_tmem;
   __shared__ uint64_t tq_full[2], tq_empty[2];
   __shared__ uint32_t tq_ph[4];
+  __shared__ int tc_unsafe;
   TcCtx tcx;
   TcBulk tq{tq_full, tq_empty, tq_ph};
   if (kTensor) {
@@ -1182,6 +1183,7 @@ __global__ void __launch_bounds__(BLR_NT, 1) k_factor(SchedParams P) {
         mbar_init(&tq_empty[s2], 1);
       }
       for (int s2 = 0; s2 < 4; s2++) tq_ph[s2] = 0;
+      tc_unsafe = 0;
     }
     tc_fence_before();
     __syncthreads();
@@ -1193,6 +1195,7 @@ __global__ void __launch_bounds__(BLR_NT, 1) k_factor(SchedParams P) {
     tcx.bcap = 256;
     tcx.status = P.status;
     tcx.limit_ns = (unsigned long long)P.watchdog_ns;
+    tcx.unsafe = &tc_unsafe;
     env.tc = &tcx;
     env.tq = &tq;
   }
@@ -1242,10 +1245,34 @@ __global__ void __launch_bounds__(BLR_NT, 1) k_factor(SchedParams P) {
     __threadfence();
     __syncthreads();
     if (threadIdx.x == 0 && type >= 0) {
-      dag_for_each_successor(d, type, i, j, k, [&](int sid) {
-        if (sid != env.skip_succ) release_task(*Pm, d, sid);
-      });
-      const unsigned long long dt = gtimer() - t_start;
+      const unsigned long long t_end = gtimer();
+      if (P.trace) {
+        const unsigned slot = atomicAdd(P.trace_n, 1u);
+        if (slot < (unsigned)P.trace_cap) {
+          unsigned smid;
+          asm volatile("mov.u32 %0, %%smid;" : "=r"(smid));
+          blr_trace_event ev;
+          ev.type = type;
+          ev.i = i;
+          ev.j = j;
+          ev.k = k;
+          ev.matrix = Pm->mat_index;
+          ev.cta = (int)blockIdx.x;
+          ev.sm = (int)smid;
+          ev.reserved = 0;
+          ev.t_start_ns = (long long)t_start;
+          ev.t_end_ns = (long long)t_end;
+          P.trace[slot] = ev;
+        }
+      }
+      // the test hook withholds every release of one task: the DAG stalls
+      // and the watchdog ends the launch
+      if (task != P.withhold) {
+        dag_for_each_successor(d, type, i, j, k, [&](int sid) {
+          if (sid != env.skip_succ) release_task(*Pm, d, sid);
+        });
+      }
+      const unsigned long long dt = t_end - t_start;
       atomicAdd(P.flops + type, 2.0 * c.fma);
       atomicAdd(P.ntask + type, 1ull);
       atomicAdd(P.tns + type, dt);
@@ -1262,7 +1289,9 @@ __global__ void __launch_bounds__(BLR_NT, 1) k_factor(SchedParams P) {
   if (kTensor) {
     tc_fence_before();
     __syncthreads();
-    if (threadIdx.x < 32) tmem_dealloc(tc_tmem, 512);
+    // an MMA or copy that could not be waited for may still use TMEM: keep it
+    // (the status already reports the timeout)
+    if (threadIdx.x < 32 && !tc_unsafe) tmem_dealloc(tc_tmem, 512);
   }
 }
 

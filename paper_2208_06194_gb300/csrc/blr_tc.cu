@@ -17,11 +17,13 @@ __global__ void __launch_bounds__(BLR_NT, 1)
   __shared__ uint64_t bars[2];
   __shared__ uint32_t phase[2];
   __shared__ uint32_t tmem_base;
+  __shared__ int unsafe;
   if (threadIdx.x < 32) tmem_alloc(&tmem_base, 256);
   if (threadIdx.x == 0) {
     mbar_init(&bars[0], 1);
     mbar_init(&bars[1], 1);
     phase[0] = phase[1] = 0;
+    unsafe = 0;
   }
   tc_fence_before();
   __syncthreads();
@@ -34,6 +36,7 @@ __global__ void __launch_bounds__(BLR_NT, 1)
   t.bcap = kTcN;
   t.status = status;
   t.limit_ns = limit_ns;
+  t.unsafe = &unsafe;
   const int mb = blockIdx.x, nb = blockIdx.y;
   const int m0 = mb * TC_M, n0 = nb * kTcN;
   const int mrow = min(TC_M, m - m0);
@@ -46,8 +49,9 @@ __global__ void __launch_bounds__(BLR_NT, 1)
       if (r < mrow && c < ncol) D[(m0 + r) + (long long)(n0 + c) * ldd] = (double)v;
     });
   }
+  tc_fence_before();
   __syncthreads();
-  if (threadIdx.x < 32) tmem_dealloc(tmem_base, 256);
+  if (threadIdx.x < 32 && !unsafe) tmem_dealloc(tmem_base, 256);
 }
 
 }  // namespace

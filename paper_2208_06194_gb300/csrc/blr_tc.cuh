@@ -205,6 +205,8 @@ struct TcCtx {
   int bcap;             // row capacity of the B staging (<= 256)
   int* status;
   unsigned long long limit_ns;
+  int* unsafe;          // shared flag: set when an issued copy or MMA could not be waited for, so
+                        // the kernel must not release TMEM or reuse the staging buffers
 };
 
 __device__ __forceinline__ size_t tc_chunk_floats(int rows) { return (size_t)rows * TC_KC; }
@@ -221,12 +223,12 @@ __device__ bool tc_gemm_tile(TcCtx& t, uint32_t col0, const GA* A, long long sar
   const size_t per = 2 * fa + 2 * fb;
   const uint32_t idesc = tc_idesc(TC_M, ncol);
   const int nchunk = (K + TC_KC - 1) / TC_KC;
-  __shared__ int skip_sh;
+  __shared__ int fail_sh;
   __syncthreads();
-  if (threadIdx.x == 0) skip_sh = (*(volatile int*)t.status & ST_TIMEOUT) != 0;
+  if (threadIdx.x == 0) fail_sh = (*(volatile int*)t.status & ST_TIMEOUT) != 0;
   __syncthreads();
-  if (skip_sh) return false;      // an earlier wait ran out: do no more tensor-core work
-  bool ok = true;
+  if (fail_sh) return false;      // an earlier wait ran out: do no more tensor-core work
+  bool pend[2] = {false, false};  // thread 0: a commit on bar[s] not yet waited for
   for (int c = 0; c < nchunk; c++) {
     const int s = c & 1;
     float* ah = t.buf + s * per;
@@ -235,9 +237,16 @@ __device__ bool tc_gemm_tile(TcCtx& t, uint32_t col0, const GA* A, long long sar
     float* bl = bh + fb;
     // the buffer was last read by the MMAs of chunk c - 2
     if (c >= 2) {
-      if (!mbar_wait(t.bar + s, t.phase[s], t.limit_ns)) ok = false;
+      if (threadIdx.x == 0) {
+        if (mbar_wait(t.bar + s, t.phase[s], t.limit_ns)) {
+          t.phase[s] ^= 1u;
+          pend[s] = false;
+        } else {
+          fail_sh = 1;
+        }
+      }
       __syncthreads();
-      if (threadIdx.x == 0) t.phase[s] ^= 1u;
+      if (fail_sh) break;         // stage nothing more into a buffer an MMA may still read
     }
     tc_stage(ah, al, A, sar, sak, TC_M, mrow, c * TC_KC, K);
     tc_stage(bh, bl, B, sbn, sbk, ncol, nrow, c * TC_KC, K);
@@ -255,19 +264,26 @@ __device__ bool tc_gemm_tile(TcCtx& t, uint32_t col0, const GA* A, long long sar
         tc_mma(t.tmem + col0, tc_desc(a0 + o), tc_desc(b0 + o), idesc, 1u);
       }
       tc_commit(t.bar + s);
+      pend[s] = true;
     }
   }
-  // drain: wait for the last one or two chunks
-  for (int c = (nchunk >= 2 ? nchunk - 2 : 0); c < nchunk; c++) {
-    const int s = c & 1;
-    if (!mbar_wait(t.bar + s, t.phase[s], t.limit_ns)) ok = false;
-    __syncthreads();
-    if (threadIdx.x == 0) t.phase[s] ^= 1u;
+  // drain every commit not yet waited for, also after a failed wait, so that
+  // no MMA still reads the staging buffers or writes TMEM after the return
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < 2; s++) {
+      if (!pend[s]) continue;
+      if (mbar_wait(t.bar + s, t.phase[s], t.limit_ns)) {
+        t.phase[s] ^= 1u;
+      } else {
+        fail_sh = 1;
+        *t.unsafe = 1;
+      }
+    }
+    if (fail_sh) atomicOr(t.status, ST_TIMEOUT);
   }
   __syncthreads();
   tc_fence_after();
-  if (!ok && threadIdx.x == 0) atomicOr(t.status, ST_TIMEOUT);
-  return ok;
+  return fail_sh == 0;
 }
 
 
@@ -379,6 +395,8 @@ __device__ bool tc_gemm_bulk(TcCtx& t, const TcBulk& q, uint32_t col0, const flo
     const uint32_t abytes = TC_M * TC_KC * 4, bbytes = (uint32_t)n * TC_KC * 4;
     const size_t per = 2 * (size_t)TC_M * TC_KC + 2 * (size_t)256 * TC_KC;   // floats per stage
     const uint32_t idesc = tc_idesc(TC_M, n);
+    bool full_pend[2] = {false, false};    // copies issued into stage s, not yet waited for
+    bool empty_pend[2] = {false, false};   // MMAs committed on stage s, not yet waited for
     auto load = [&](int c, int s) {
       float* ah = t.buf + s * per;
       float* al = ah + TC_M * TC_KC;
@@ -389,6 +407,7 @@ __device__ bool tc_gemm_bulk(TcCtx& t, const TcBulk& q, uint32_t col0, const flo
       bulk_g2s(al, a_lo + c * a_cs, abytes, q.full + s);
       bulk_g2s(bh, b_hi + c * b_cs, bbytes, q.full + s);
       bulk_g2s(bl, b_lo + c * b_cs, bbytes, q.full + s);
+      full_pend[s] = true;
     };
     const int nc_run = ok ? nchunk : 0;
     for (int c = 0; c < nc_run && c < 2; c++) load(c, c);
@@ -396,6 +415,7 @@ __device__ bool tc_gemm_bulk(TcCtx& t, const TcBulk& q, uint32_t col0, const flo
       const int s = c & 1;
       if (!mbar_wait(q.full + s, q.ph[s], t.limit_ns)) { ok = false; break; }
       q.ph[s] ^= 1u;
+      full_pend[s] = false;
       tc_fence_after();
       const uint32_t a0 = smem_u32(t.buf + s * per), a1 = a0 + abytes, b0 = a1 + abytes, b1 = b0 + 256 * TC_KC * 4;
 #pragma unroll
@@ -406,19 +426,34 @@ __device__ bool tc_gemm_bulk(TcCtx& t, const TcBulk& q, uint32_t col0, const flo
         tc_mma(t.tmem + col0, tc_desc(a0 + o), tc_desc(b0 + o), idesc, 1u);
       }
       tc_commit(q.empty + s);
-      if (c + 2 < nchunk) {
-        if (!mbar_wait(q.empty + s, q.ph[2 + s], t.limit_ns)) { ok = false; break; }
-        q.ph[2 + s] ^= 1u;
-        load(c + 2, s);
+      empty_pend[s] = true;
+      // refill the other stage with chunk c + 1 once the MMAs of chunk c - 1
+      // (its last reader) are done; chunk c's MMAs stay queued meanwhile
+      if (c >= 1 && c + 1 < nchunk) {
+        const int o2 = s ^ 1;
+        if (!mbar_wait(q.empty + o2, q.ph[2 + o2], t.limit_ns)) { ok = false; break; }
+        q.ph[2 + o2] ^= 1u;
+        empty_pend[o2] = false;
+        load(c + 1, o2);
       }
     }
-    // the last one or two commits (their stages are not reloaded)
-    if (ok) {
-      for (int c = (nc_run >= 2 ? nc_run - 2 : 0); c < nc_run; c++) {
-        const int s = c & 1;
-        if (!mbar_wait(q.empty + s, q.ph[2 + s], t.limit_ns)) { ok = false; break; }
-        q.ph[2 + s] ^= 1u;
+    // drain: every commit and copy not yet waited for (normally the last one
+    // or two commits; after a failed wait, whatever is still in flight), so
+    // that nothing writes the staging buffers or TMEM after the return
+    bool drained = true;
+    for (int s = 0; s < 2; s++) {
+      if (empty_pend[s]) {
+        if (mbar_wait(q.empty + s, q.ph[2 + s], t.limit_ns)) q.ph[2 + s] ^= 1u;
+        else drained = false;
       }
+      if (full_pend[s]) {
+        if (mbar_wait(q.full + s, q.ph[s], t.limit_ns)) q.ph[s] ^= 1u;
+        else drained = false;
+      }
+    }
+    if (!drained) {
+      ok = false;
+      *t.unsafe = 1;
     }
     if (!ok) atomicOr(t.status, ST_TIMEOUT);
     ok_sh = ok && nc_run == nchunk;

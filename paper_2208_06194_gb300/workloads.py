@@ -124,14 +124,22 @@ def ill_conditioned_scale(n: int) -> np.ndarray:
 
 
 def kernel_problem(kernel: str, m: int, n: int, b: int, seed_x: int, seed_y: int,
-                   ill_conditioned: bool = False) -> KernelProblem:
+                   ill_conditioned: bool = False, extent=None) -> KernelProblem:
     """Seeded kernel-matrix workload.
 
-    1D points are sorted ascending; 3D points are RCB-ordered with leaf size b.
+    Points are uniform in the unit box, or in the box [0, extent[d]] per
+    coordinate when extent is given (a stretched domain gives a small matrix
+    the mix of near, mid and far tiles that the unit cube gives only at large
+    sizes).  1D points are sorted ascending; 3D points are RCB-ordered with
+    leaf size b.
     """
     dim = KERNEL_DIM[kernel]
     x = np.random.default_rng(seed_x).random((dim, m))
     y = np.random.default_rng(seed_y).random((dim, n))
+    if extent is not None:
+        e = np.asarray(extent, dtype=np.float64).reshape(dim, 1)
+        x = x * e
+        y = y * e
     if dim == 1:
         x = np.sort(x, axis=1)
         y = np.sort(y, axis=1)

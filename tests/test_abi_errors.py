@@ -149,6 +149,10 @@ def test_qr_entry_points_reject_on_host(L):
     nortol = _opts(b=128, tol=0.0, rec_tol=0.0)
     assert L.blr_batch_plan_create(arr, 2, ctypes.byref(nortol), ctypes.byref(plan), None) == INVALID
     assert "rec_tol" in blr.blr_last_error()
+    for kw, msg in [({"trace": -1}, "trace"), ({"test_withhold": -3}, "test_withhold")]:
+        neg = _opts(b=128, **kw)
+        assert L.blr_batch_plan_create(arr, 2, ctypes.byref(neg), ctypes.byref(plan), None) == INVALID
+        assert msg in blr.blr_last_error()
     assert L.blr_batch_plan_launch(None, None) == INVALID
     assert L.blr_batch_plan_finish(None, None) == INVALID
     assert L.blr_batch_plan_factor(None, 0) is None
@@ -173,6 +177,15 @@ def test_solve_entry_points_reject_null_handles(L):
     assert L.blr_stats(None, 0, ctypes.byref(st)) == INVALID
     clone = _P()
     assert L.blr_matrix_clone(None, ctypes.byref(clone), None) == INVALID
+    # blr_densify: NULL handle or output, which out of range, R / Y~ of a matrix
+    assert L.blr_densify(None, 0, 0, fake, 128, None) == INVALID
+    assert L.blr_densify(fake, 0, 0, None, 128, None) == INVALID
+    assert L.blr_densify(fake, 1, 3, fake, 128, None) == INVALID
+    assert L.blr_densify(fake, 0, 1, fake, 128, None) == INVALID
+    assert "matrix handle" in blr.blr_last_error()
+    # blr_trace_export: NULL factor, or no buffer for a positive capacity
+    assert L.blr_trace_export(None, None, 0, None) == -1
+    assert L.blr_trace_export(fake, None, 4, None) == -1
 
 
 def test_tc_selftest_rejects_on_host(L):

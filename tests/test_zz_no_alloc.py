@@ -1,9 +1,11 @@
 """blr_apply_qt_noalloc: the allocation-free variant of blr_apply_qt for
-callers that cannot allocate device memory during a call (allocation-free
-stream captures, application-owned memory pools, latency-critical solvers).
-It must give the allocating call's result, on consecutive calls that reuse
-its static scratch, and reject right-hand-side counts beyond that scratch.
-Collected last so that a failure here does not stop the other tests."""
+callers that cannot allocate device memory during a call (applications that
+own all device memory through their own pool, latency-critical solvers that
+cannot afford the allocator's implicit synchronisation).  It must give the
+allocating call's result, on consecutive calls that reuse its static
+scratch, accept right-hand-side counts up to what that scratch holds and
+reject one column group more.  Collected last so that a failure here does
+not stop the other tests."""
 import numpy as np
 import pytest
 
@@ -34,5 +36,22 @@ def test_apply_qt_noalloc_matches_allocating_call(lib):
     big = lib.fortran_empty(m, 8192)   # 1024 column groups x 4.6 KB > 4 MiB at b = 64
     with pytest.raises(lib.BLRError) as e:
         lib.blr_apply_qt_noalloc(fac, big, trans=0)
+    assert e.value.code == 1
+    # the exact limit of the documented formula: 256 bytes + q*8 rounded up
+    # to 256 + ceil(nrhs/8) * (16 (b/2) + 64) * 8 bytes <= 4 MiB
+    q = n // b
+    fixed = 256 + (q * 8 + 255) // 256 * 256
+    per_group = (16 * (b // 2) + 64) * 8
+    groups = (4 * 2 ** 20 - fixed) // per_group
+    nmax = groups * 8
+    c = rng.standard_normal((m, nmax))
+    want = lib.to_fortran(torch.from_numpy(c))
+    lib.blr_apply_qt(fac, want, trans=0)
+    got = lib.to_fortran(torch.from_numpy(c))
+    lib.blr_apply_qt_noalloc(fac, got, trans=0)                 # the largest accepted count works
+    assert float(torch.linalg.norm(got - want) / torch.linalg.norm(want)) <= 1e-13
+    over = lib.fortran_empty(m, nmax + 1)                       # one more column group
+    with pytest.raises(lib.BLRError) as e:
+        lib.blr_apply_qt_noalloc(fac, over, trans=0)
     assert e.value.code == 1
     fac.destroy()
