@@ -33,22 +33,48 @@ import numpy as np  # noqa: E402
 
 METRIC = "BLR-QR sec & %roofline at 65k x 32k; mixed vs FP64 GPU at stated ||A-QR||/||A||"
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
-# FP64 ALU peak for the roofline: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz
-# (the nominal 1.25 TFLOP/s FP64 of GB300); FP32 SIMT: 152 x 128 x 2 x 2.07 GHz.
-FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
-FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
-# TF32 tensor peak: the measured dense bf16 rate x the nominal TF32/BF16 ratio
-# (1.1 / 2.25 PFLOP/s); a 3xTF32 product issues three MMAs, so the rate of
-# algorithmic flops is a third of it.
-TF32_OVER_BF16 = 1.1 / 2.25
+# Arithmetic peaks of the pipes this path runs on, measured on a GB300 of
+# this pool (one GPU, CUDA events, best of 5-8):
+#   FP64: a DFMA throughput loop (16 independent register chains per thread,
+#         152 x 8 CTAs of 256 threads): 1.255 TFLOP/s (cuBLAS DGEMM 8192^3:
+#         1.10);
+#   FP32 SIMT: the same loop in FFMA: 76.7 TFLOP/s;
+#   TF32 tensor: torch.matmul of 8192^3 float32 with TF32 allowed (cuBLAS):
+#         1033 TFLOP/s; a 3xTF32 product issues three MMAs, so the rate of
+#         algorithmic flops is a third of it.
+FP64_PEAK_TFLOPS = 1.255
+FP32_PEAK_TFLOPS = 76.7
+TF32_PEAK_TFLOPS = 1033.0
+TC_KINDS = (2, 3, 5, 6, 7)   # update kinds applied on the tensor cores (see roofline)
+# DRAM traffic of the factorization kernel: a summary of one ncu capture
+# (profiles/), valid while the kernel sources it names are unchanged.
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "k_factor_mixed_traffic_yukawa3d.md")
 
 
-def measured_bf16_tflops():
+def csrc_digest() -> str:
+    """sha256 (16 hex digits) of the CUDA sources of the library."""
+    import hashlib
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_2208_06194_gb300", "csrc")
+    for name in sorted(os.listdir(d)):
+        with open(os.path.join(d, name), "rb") as fh:
+            h.update(name.encode() + b"\0" + fh.read())
+    return h.hexdigest()[:16]
+
+
+def dram_traffic(flops_counted: float):
+    """Bytes of DRAM traffic per launch, scaled from the committed ncu
+    capture by counted flops; None when the kernel changed since."""
     try:
-        with open(PEAKS_FILE) as fh:
-            return float(json.load(fh)["bf16_tflops"]), "measured"
-    except (OSError, KeyError, ValueError):
-        return 1900.0, "fallback"
+        text = open(TRAFFIC_FILE).read()
+    except OSError:
+        return None, "no capture"
+    fields = dict(line.strip("- ").split(": ", 1) for line in text.splitlines()
+                  if line.startswith("- ") and ": " in line)
+    if fields.get("csrc_sha16") != csrc_digest():
+        return None, "the kernel changed since the committed capture"
+    per_flop = float(fields["dram_bytes_per_counted_flop"])
+    return per_flop * flops_counted, f"scaled by counted flops from {fields.get('workload', '?')}"
 
 
 def roofline(st, k_sec, prec_is_fp64):
@@ -62,25 +88,27 @@ def roofline(st, k_sec, prec_is_fp64):
     if prec_is_fp64:
         peak = FP64_PEAK_TFLOPS
         return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": None, "peak_note": "FP64 ALU nominal 1.26 TFLOP/s (152 SMs x 2 DFMA/clk x 2.07 GHz)",
+                "traffic": None,
+                "peak_note": "FP64 ALU, measured DFMA throughput 1.255 TFLOP/s (of measured)",
                 "kernel": "k_factor (persistent scheduler)", "flops_counted": flops}
-    bf16, src = measured_bf16_tflops()
-    p_tc = bf16 * TF32_OVER_BF16 / 3.0
+    p_tc = TF32_PEAK_TFLOPS / 3.0
     # updates whose reflector block is applied on the tensor cores: Y~ dense
     # with a dense R_kj or A_ij, and Y~ low-rank with a dense R_kj (their
     # rounded additions, a small share, are counted at the tensor rate too,
     # which can only lower the reported fraction)
-    f_tc = sum(st["tpmqrt_kind_flops"][v] for v in (2, 3, 5, 6, 7))
+    f_tc = sum(st["tpmqrt_kind_flops"][v] for v in TC_KINDS)
     t_bound = f_tc / (p_tc * 1e12) + (flops - f_tc) / (FP32_PEAK_TFLOPS * 1e12)
     peak = flops / t_bound / 1e12
+    traffic, traffic_note = dram_traffic(flops)
     return {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": t_bound / k_sec,
-            "traffic": None,
+            "traffic": traffic, "traffic_note": traffic_note,
             "peak_note": (f"mix of this run: {f_tc / 1e12:.1f} TFLOP at the 3xTF32 rate ({p_tc:.0f} TFLOP/s = "
-                          f"{src} bf16 {bf16:.0f} x 1.1/2.25 / 3) + {(flops - f_tc) / 1e12:.1f} TFLOP at the FP32 "
-                          f"SIMT rate ({FP32_PEAK_TFLOPS:.1f} TFLOP/s); peak = flops / summed bound time"),
+                          f"measured TF32 {TF32_PEAK_TFLOPS:.0f} / 3) + {(flops - f_tc) / 1e12:.1f} TFLOP at the "
+                          f"measured FP32 SIMT rate ({FP32_PEAK_TFLOPS:.1f} TFLOP/s); peak = flops / summed bound "
+                          f"time (of measured)"),
             "kernel": "k_factor (persistent scheduler)", "flops_counted": flops,
             "tensor_part": {"tflop": f_tc / 1e12,
-                            "cta_seconds": sum(st["tpmqrt_kind_seconds"][v] for v in (2, 3, 5, 6, 7))}}
+                            "cta_seconds": sum(st["tpmqrt_kind_seconds"][v] for v in TC_KINDS)}}
 
 SIZES = {
     "full": dict(m=65536, n=32768, b=512, seed_x=301, seed_y=302),
@@ -109,6 +137,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-compare-fp64", action="store_true",
                     help="skip the FP64 factorization timed beside the mixed one (N = 1)")
+    ap.add_argument("--fp64-steps", type=int, default=3, help="timed FP64 factorizations (median)")
+    ap.add_argument("--fp64-warmup", type=int, default=1)
     ap.add_argument("--scratch-b2", type=int, default=0, help="per-CTA scratch in units of b*b doubles")
     ap.add_argument("--workload", default="yukawa", choices=["yukawa", "batched"],
                     help="batched: 64 uneven Laplace 3D matrices in one graph-captured launch")
@@ -225,34 +255,53 @@ def dense_equivalent(m: int, n: int, seconds: float) -> dict:
             "note": "context only: (2mn^2 - 2n^3/3) / time, the work of a dense Householder QR"}
 
 
-def tpmqrt_kinds(st):
+def tpmqrt_kinds(st, prec_is_fp64=False):
     """Trapezoidal updates by operand kinds (D dense, L low-rank) of Y~_ik,
-    R_kj and A_ij: count, summed CTA-seconds, counted GFLOP."""
+    R_kj and A_ij: count, summed CTA-seconds, counted GFLOP, and the rate
+    while they run as a fraction of one SM's share of the pipe they run on
+    (3xTF32 tensor, FP32 SIMT or FP64; one CTA per SM)."""
     out = {}
     for v in range(8):
         n = st["tpmqrt_kind"][v]
         if n:
             name = "Y{} R{} A{}".format(*("D" if v & bit else "L" for bit in (4, 2, 1)))
-            out[name] = {"n": n, "cta_s": round(st["tpmqrt_kind_seconds"][v], 3),
-                         "gflop": round(st["tpmqrt_kind_flops"][v] / 1e9, 1)}
+            cta_s, fl = st["tpmqrt_kind_seconds"][v], st["tpmqrt_kind_flops"][v]
+            if prec_is_fp64:
+                pipe, peak = "fp64", FP64_PEAK_TFLOPS
+            elif v in TC_KINDS:
+                pipe, peak = "3xtf32", TF32_PEAK_TFLOPS / 3.0
+            else:
+                pipe, peak = "fp32", FP32_PEAK_TFLOPS
+            rate = fl / cta_s / 1e9 if cta_s > 0 else 0.0
+            out[name] = {"n": n, "cta_s": round(cta_s, 3), "gflop": round(fl / 1e9, 1),
+                         "gflops_per_sm": round(rate, 1), "pipe": pipe,
+                         "frac_of_sm_peak": round(rate / (peak * 1e3 / 152), 4)}
     return out
 
 
-def cpu_baseline(pr_args, tol):
-    """The oracle as it stands on the host cores, on a bounded sample: the
-    leading 16 x 2 tiles of the same matrix (compressed once by the oracle,
-    not timed), factored by the oracle's Algorithm 4 with per-task timers;
-    the mean time per task type is scaled by the task counts of the full
-    factorization."""
+def _task_counts(p: int, q: int) -> dict:
+    return {"geqrt": q, "larfb": q * (q - 1) // 2,
+            "tsqrt": sum(p - k - 1 for k in range(q)),
+            "tpmqrt": sum((p - k - 1) * (q - k - 1) for k in range(q))}
+
+
+def _host_cores() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def oracle_factor_time(m: int, n: int, b: int, tol: float, dense_rank: int, seeds: tuple) -> dict:
+    """The oracle as it stands on one whole matrix of the benchmark's
+    generator: compression (not timed), then Algorithm 4 timed in full, with
+    the time of every task recorded by type."""
     from oracle import blr_qr as O
     from paper_2208_06194_gb300 import workloads as W
-    b = pr_args["b"]
-    ps, qs = 16, 2
-    key = (tuple(sorted(pr_args.items())), tol)
+    key = (m, n, b, tol, dense_rank, seeds)
     if key not in _SAMPLE:
-        pr = W.yukawa3d(pr_args["m"], pr_args["n"], b, pr_args["seed_x"], pr_args["seed_y"])
-        _SAMPLE[key] = O.compress(pr.tile, ps, qs, b, eps=tol)
-    sub = _SAMPLE[key]
+        pr = W.yukawa3d(m, n, b, *seeds)
+        _SAMPLE[key] = O.compress(pr.tile, m // b, n // b, b, eps=tol, dense_rank=dense_rank)
     times = {"geqrt": [], "larfb": [], "tsqrt": [], "tpmqrt": []}
 
     def timed(name, fn):
@@ -268,42 +317,85 @@ def cpu_baseline(pr_args, tol):
                                            timed("tsqrt", O.tsqrt), timed("tpmqrt", O.tpmqrt))
     t0 = time.perf_counter()
     try:
-        O.blr_qr(sub, tol)
+        O.blr_qr(_SAMPLE[key], tol)
     finally:
         O.geqrt, O.larfb, O.tsqrt, O.tpmqrt = saved
     wall = time.perf_counter() - t0
+    return {"workload": f"yukawa3d {m}x{n} b={b} tol={tol:g} dense threshold {dense_rank}", "seconds": wall,
+            "mean_task_s": {t: (statistics.mean(v) if v else 0.0) for t, v in times.items()},
+            "tasks": {t: len(v) for t, v in times.items()}}
+
+
+def extrapolate(sample: dict, p: int, q: int) -> float:
+    """Mean oracle time per task type of a fully timed run x the task counts
+    of a p x q tile DAG (the work outside the tasks is negligible)."""
+    counts = _task_counts(p, q)
+    return sum(counts[t] * sample["mean_task_s"][t] for t in counts)
+
+
+def cpu_baseline(pr_args, tol, dense_rank):
+    """The oracle on the host cores, timed in full on two smaller matrices of
+    the same generator, tolerance and dense threshold (4096 x 2048 and
+    8192 x 4096), and on the 2048 x 1024 fixed-rank workload.  The value for
+    the 65536 x 32768 factorization is extrapolated from the 8192 x 4096 run
+    (mean time per task type x the full task counts: at this threshold
+    nearly every tile of both is dense, so a task costs the same in both);
+    the same extrapolation from 4096 x 2048 to 8192 x 4096 is checked
+    against the timed run."""
+    from oracle import blr_qr as O
+    from paper_2208_06194_gb300 import workloads as W
+    b = pr_args["b"]
+    seeds = (pr_args["seed_x"], pr_args["seed_y"])
+    small = oracle_factor_time(4096, 2048, b, tol, dense_rank, seeds)
+    mid = oracle_factor_time(8192, 4096, b, tol, dense_rank, seeds)
+    predicted_mid = extrapolate(small, 8192 // b, 4096 // b)
     p, q = pr_args["m"] // b, pr_args["n"] // b
-    counts = {"geqrt": q, "larfb": q * (q - 1) // 2,
-              "tsqrt": sum(p - k - 1 for k in range(q)),
-              "tpmqrt": sum((p - k - 1) * (q - k - 1) for k in range(q))}
-    est = sum(counts[t] * (statistics.mean(v) if v else 0.0) for t, v in times.items())
-    try:
-        cores = len(os.sched_getaffinity(0))
-    except AttributeError:
-        cores = os.cpu_count()
-    return {"value": est, "unit": "s", "cores": cores, "kind": "oracle",
-            "sample": (f"oracle Algorithm 4 on the leading {ps}x{qs} tiles of the same matrix "
-                       f"({wall:.1f} s wall; tasks timed: " +
-                       ", ".join(f"{k} {len(v)}" for k, v in times.items()) +
-                       "); mean time per task type x task counts of the full factorization"),
-            "threads": os.environ.get("OMP_NUM_THREADS", "numpy default")}
+    est = extrapolate(mid, p, q)
+    pr1 = W.inv1d_2048x1024()
+    a1 = O.compress(pr1.tile, 16, 8, 128, fixed_rank=8)
+    t0 = time.perf_counter()
+    O.blr_qr(a1, 1e-14)
+    cfg1 = time.perf_counter() - t0
+    cores = _host_cores()
+    return {"value": est, "unit": "s", "cores": cores, "kind": "oracle_extrapolated",
+            "threads": os.environ.get("OMP_NUM_THREADS", f"numpy BLAS default ({cores} host cores)"),
+            "sample": (f"oracle Algorithm 4 timed in full on {mid['workload']} ({mid['seconds']:.1f} s, "
+                       f"{sum(mid['tasks'].values())} tasks); its mean time per task type x the task counts "
+                       f"of the {pr_args['m']}x{pr_args['n']} factorization"),
+            "timed_full": [{"workload": small["workload"], "seconds": small["seconds"]},
+                           {"workload": mid["workload"], "seconds": mid["seconds"]},
+                           {"workload": "inv1d 2048x1024 b=128 fixed rank 8 (rec 1e-14)", "seconds": cfg1}],
+            "extrapolation_check": {"from": small["workload"], "to": mid["workload"],
+                                    "predicted_s": predicted_mid, "timed_s": mid["seconds"],
+                                    "error": predicted_mid / mid["seconds"] - 1.0}}
 
 
 # ----------------------------------------------------------------------------- main
 def run_reference(args, rank, world):
-    """Reference arm: the oracle (the only reference there is) on the host."""
+    """Reference arm: the oracle (the only reference there is) on the host.
+    Each step times the oracle in full on the 4096 x 2048 matrix of the same
+    generator, tolerance and dense threshold and extrapolates it to the
+    benchmark's size (mean time per task type x the full task counts)."""
     if rank != 0:
         return
-    res = []
-    for _ in range(args.warmup + args.steps):
-        res.append(cpu_baseline(SIZES[args.size], args.tol))
-    vals = [r["value"] for r in res[args.warmup:]]
+    s = SIZES[args.size]
+    b = s["b"]
+    vals, last = [], None
+    for it in range(args.warmup + args.steps):
+        last = oracle_factor_time(4096, 2048, b, args.tol, args.dense_rank, (s["seed_x"], s["seed_y"]))
+        if it >= args.warmup:
+            vals.append(extrapolate(last, s["m"] // b, s["n"] // b))
     v = statistics.median(vals)
+    cores = _host_cores()
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": v * 1e3,
             "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": workload_name(args), "global_batch": 1},
-            "cpu_baseline": {k: res[-1][k] for k in ("kind", "cores", "sample")} | {"value": v, "unit": "s"},
+            "data": "synthetic",
+            "config": {"workload": workload_name(args), "global_batch": 1, "dense_rank": args.dense_rank},
+            "cpu_baseline": {"kind": "oracle_extrapolated", "cores": cores, "value": v, "unit": "s",
+                             "sample": (f"per step: oracle Algorithm 4 timed in full on {last['workload']} "
+                                        f"({last['seconds']:.1f} s); mean time per task type x the task counts of "
+                                        f"the {s['m']}x{s['n']} factorization")},
             "e2e": {"value": v, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -486,12 +578,23 @@ def main():
         o64 = blr.blr_opts_default(b=s["b"], tol=args.tol, precision=blr.BLR_PREC_FP64,
                                    dense_rank=args.dense_rank_fp64, scratch_b2=args.scratch_b2)
         a64 = blr.blr_compress_kernel(pr.x, pr.y, "yukawa3d", o64, col_scale=pr.col_scale)   # its own threshold
-        f64, t64 = one_step(o64, a64)
+        for _ in range(args.fp64_warmup):
+            f64, _t = one_step(o64, a64)
+            f64.destroy()
+        t64s, f64 = [], None
+        for _ in range(max(1, args.fp64_steps)):
+            if f64 is not None:
+                f64.destroy()
+            f64, t64 = one_step(o64, a64)
+            t64s.append(t64)
+        t64 = statistics.median(t64s)
         r64 = probes(blr, f64, a64, pr, torch, dev)
         st64 = blr.blr_stats(f64)
         a64.destroy()
-        fp64 = {"seconds": t64, "res_A": r64[0], "res_At": r64[1], "orth": r64[2],
+        fp64 = {"seconds": t64, "seconds_all": t64s, "warmup": args.fp64_warmup,
+                "res_A": r64[0], "res_At": r64[1], "orth": r64[2],
                 "gflops_counted": st64["flops"][4] / 1e9,
+                "roofline": roofline(st64, statistics.median(t64s), True),
                 "meets_10tol": bool(r64[0] <= 10 * args.tol), "mixed_speedup": t64 / t_step,
                 "dense_rank": args.dense_rank_fp64}
         f64.destroy()
@@ -525,7 +628,7 @@ def main():
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
-        cpu = cpu_baseline(s, args.tol)
+        cpu = cpu_baseline(s, args.tol, args.dense_rank)
 
     if rank != 0:
         if world > 1:
@@ -546,7 +649,7 @@ def main():
                   "after": {"n_dense": st["n_dense"], "mean": st["mean_rank"], "max": st["max_rank"]}},
         "kernel_seconds": k_sec,
         "task_cta_seconds": dict(zip(["geqrt", "larfb", "tsqrt", "tpmqrt"], st["task_seconds"])),
-        "tpmqrt_kinds": tpmqrt_kinds(st),
+        "tpmqrt_kinds": tpmqrt_kinds(st, prec == blr.BLR_PREC_FP64),
         "dense_equivalent": dense_equivalent(s["m"], s["n"], t_step),
         "roofline": roofline(st, k_sec, prec == blr.BLR_PREC_FP64),
         "clocks": clk,

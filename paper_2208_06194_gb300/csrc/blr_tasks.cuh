@@ -330,13 +330,9 @@ __device__ void tsqrt_prep(TaskEnv& env, int i, int k, Ctx& c) {
     for (int n0 = 0; n0 < b; n0 += 256) {
       if (n0 + 256 <= m0) continue;       // strictly below the diagonal: not needed
       const int nn = min(256, b - n0), nn16 = (nn + 15) & ~15;
-      tc_gemm_bulk(tc, *env.tq, n0, yt_h + (size_t)m0 * TC_KC, yt_l + (size_t)m0 * TC_KC, cs,
+      tc_gemm_bulk(tc, *env.tq, 0, yt_h + (size_t)m0 * TC_KC, yt_l + (size_t)m0 * TC_KC, cs,
                    yt_h + (size_t)n0 * TC_KC, yt_l + (size_t)n0 * TC_KC, cs, nn16, Kt / TC_KC);
-    }
-    for (int n0 = 0; n0 < b; n0 += 256) {
-      if (n0 + 256 <= m0) continue;
-      const int nn = min(256, b - n0), nn16 = (nn + 15) & ~15;
-      tc_epilogue(tc, n0, nn16, [&](int r, int col, float v) {
+      tc_epilogue(tc, 0, nn16, [&](int r, int col, float v) {
         if (m0 + r < b && col < nn) G[(m0 + r) + (size_t)(n0 + col) * b] = v;
       });
     }
@@ -405,14 +401,11 @@ __device__ void tc_apply_prepared(TaskEnv& env, const float* slot, double* Ct, d
   for (int m0 = 0; m0 < b; m0 += TC_M) {
     for (int n0 = 0; n0 < b; n0 += 256) {
       const int nn = min(256, b - n0), nn16 = (nn + 15) & ~15;
-      PH(13, tc_gemm_bulk(tc, q, n0, yt_h + (size_t)m0 * TC_KC, yt_l + (size_t)m0 * TC_KC, cs, cc_h + (size_t)n0 * TC_KC,
+      PH(13, tc_gemm_bulk(tc, q, 0, yt_h + (size_t)m0 * TC_KC, yt_l + (size_t)m0 * TC_KC, cs, cc_h + (size_t)n0 * TC_KC,
                    cc_l + (size_t)n0 * TC_KC, cs, nn16, nchunk));
-    }
-    for (int n0 = 0; n0 < b; n0 += 256) {
-      const int nn = min(256, b - n0), nn16 = (nn + 15) & ~15;
       {
       PH_BEGIN();
-      tc_epilogue16(tc, n0, nn16, [&](int r, int col, const float* v) {
+      tc_epilogue16(tc, 0, nn16, [&](int r, int col, const float* v) {
         const int a = m0 + r;
         if (a >= b) return;
         double ct[16];
@@ -433,14 +426,11 @@ __device__ void tc_apply_prepared(TaskEnv& env, const float* slot, double* Ct, d
     const int kch = min(b, m0 + TC_M) / TC_KC;
     for (int n0 = 0; n0 < b; n0 += 256) {
       const int nn = min(256, b - n0), nn16 = (nn + 15) & ~15;
-      PH(13, tc_gemm_bulk(tc, q, n0, tt_h + (size_t)m0 * TC_KC, tt_l + (size_t)m0 * TC_KC, cs, zc_h + (size_t)n0 * TC_KC,
+      PH(13, tc_gemm_bulk(tc, q, 0, tt_h + (size_t)m0 * TC_KC, tt_l + (size_t)m0 * TC_KC, cs, zc_h + (size_t)n0 * TC_KC,
                    zc_l + (size_t)n0 * TC_KC, cs, nn16, kch));
-    }
-    for (int n0 = 0; n0 < b; n0 += 256) {
-      const int nn = min(256, b - n0), nn16 = (nn + 15) & ~15;
       {
       PH_BEGIN();
-      tc_epilogue16(tc, n0, nn16, [&](int r, int col, const float* v) {
+      tc_epilogue16(tc, 0, nn16, [&](int r, int col, const float* v) {
         const int a = m0 + r;
         if (a >= b) return;
         double ct[16];
@@ -464,14 +454,11 @@ __device__ void tc_apply_prepared(TaskEnv& env, const float* slot, double* Ct, d
   for (int m0 = 0; m0 < b; m0 += TC_M) {
     for (int n0 = 0; n0 < b; n0 += 256) {
       const int nn = min(256, b - n0), nn16 = (nn + 15) & ~15;
-      PH(13, tc_gemm_bulk(tc, q, n0, yc_h + (size_t)m0 * TC_KC, yc_l + (size_t)m0 * TC_KC, cs, cc_h + (size_t)n0 * TC_KC,
+      PH(13, tc_gemm_bulk(tc, q, 0, yc_h + (size_t)m0 * TC_KC, yc_l + (size_t)m0 * TC_KC, cs, cc_h + (size_t)n0 * TC_KC,
                    cc_l + (size_t)n0 * TC_KC, cs, nn16, nchunk));
-    }
-    for (int n0 = 0; n0 < b; n0 += 256) {
-      const int nn = min(256, b - n0), nn16 = (nn + 15) & ~15;
       {
       PH_BEGIN();
-      tc_epilogue16(tc, n0, nn16, [&](int r, int col, const float* v) {
+      tc_epilogue16(tc, 0, nn16, [&](int r, int col, const float* v) {
         const int rr = m0 + r;
         if (rr >= b) return;
         double cb[16];
@@ -521,12 +508,9 @@ __device__ void tc_apply_lr_prepared(TaskEnv& env, const float* slot, int ry, fl
   for (int m0 = 0; m0 < b; m0 += TC_M) {
     for (int n0 = 0; n0 < b; n0 += 256) {
       const int nn = min(256, b - n0), nn16 = (nn + 15) & ~15;
-      tc_gemm_bulk(tc, q, n0, yt_h + (size_t)m0 * TC_KC, yt_l + (size_t)m0 * TC_KC, cs, pc_h + (size_t)n0 * TC_KC,
+      tc_gemm_bulk(tc, q, 0, yt_h + (size_t)m0 * TC_KC, yt_l + (size_t)m0 * TC_KC, cs, pc_h + (size_t)n0 * TC_KC,
                    pc_l + (size_t)n0 * TC_KC, cs, nn16, Kt / TC_KC);
-    }
-    for (int n0 = 0; n0 < b; n0 += 256) {
-      const int nn = min(256, b - n0), nn16 = (nn + 15) & ~15;
-      tc_epilogue16(tc, n0, nn16, [&](int r, int col, const float* v) {
+      tc_epilogue16(tc, 0, nn16, [&](int r, int col, const float* v) {
         const int a = m0 + r;
         if (a >= b) return;
         float ct[16];
@@ -545,12 +529,9 @@ __device__ void tc_apply_lr_prepared(TaskEnv& env, const float* slot, int ry, fl
     const int kch = min(b, m0 + TC_M) / TC_KC;
     for (int n0 = 0; n0 < b; n0 += 256) {
       const int nn = min(256, b - n0), nn16 = (nn + 15) & ~15;
-      tc_gemm_bulk(tc, q, n0, tt_h + (size_t)m0 * TC_KC, tt_l + (size_t)m0 * TC_KC, cs, zc_h + (size_t)n0 * TC_KC,
+      tc_gemm_bulk(tc, q, 0, tt_h + (size_t)m0 * TC_KC, tt_l + (size_t)m0 * TC_KC, cs, zc_h + (size_t)n0 * TC_KC,
                    zc_l + (size_t)n0 * TC_KC, cs, nn16, kch);
-    }
-    for (int n0 = 0; n0 < b; n0 += 256) {
-      const int nn = min(256, b - n0), nn16 = (nn + 15) & ~15;
-      tc_epilogue16(tc, n0, nn16, [&](int r, int col, const float* v) {
+      tc_epilogue16(tc, 0, nn16, [&](int r, int col, const float* v) {
         const int a = m0 + r;
         if (a >= b) return;
         float ct[16];
@@ -572,12 +553,9 @@ __device__ void tc_apply_lr_prepared(TaskEnv& env, const float* slot, int ry, fl
   for (int m0 = 0; m0 < ry; m0 += TC_M) {
     for (int n0 = 0; n0 < b; n0 += 256) {
       const int nn = min(256, b - n0), nn16 = (nn + 15) & ~15;
-      tc_gemm_bulk(tc, q, n0, yc_h + (size_t)m0 * TC_KC, yc_l + (size_t)m0 * TC_KC, cs_s, wc_h + (size_t)n0 * TC_KC,
+      tc_gemm_bulk(tc, q, 0, yc_h + (size_t)m0 * TC_KC, yc_l + (size_t)m0 * TC_KC, cs_s, wc_h + (size_t)n0 * TC_KC,
                    wc_l + (size_t)n0 * TC_KC, cs, nn16, b / TC_KC);
-    }
-    for (int n0 = 0; n0 < b; n0 += 256) {
-      const int nn = min(256, b - n0), nn16 = (nn + 15) & ~15;
-      tc_epilogue16(tc, n0, nn16, [&](int r, int col, const float* v) {
+      tc_epilogue16(tc, 0, nn16, [&](int r, int col, const float* v) {
         const int s = m0 + r;
         if (s >= ry) return;
 #pragma unroll
@@ -865,11 +843,8 @@ __device__ void tc_densify(TaskEnv& env, const double* Tl, int r, double* D, Ctx
     const int mrow = min(TC_M, b - r0);
     for (int n0 = 0; n0 < b; n0 += 256) {
       const int nn = min(256, b - n0), nn16 = (nn + 15) & ~15;
-      tc_gemm_tile(tc, n0, U + r0, 1, b, mrow, V + n0, 1, b, nn, nn16, r);
-    }
-    for (int n0 = 0; n0 < b; n0 += 256) {
-      const int nn = min(256, b - n0), nn16 = (nn + 15) & ~15;
-      tc_epilogue(tc, n0, nn16, [&](int rr, int cc, float v) {
+      tc_gemm_tile(tc, 0, U + r0, 1, b, mrow, V + n0, 1, b, nn, nn16, r);
+      tc_epilogue(tc, 0, nn16, [&](int rr, int cc, float v) {
         if (rr < mrow && cc < nn) D[(r0 + rr) + (size_t)(n0 + cc) * b] = cvt<double>(v);
       });
     }
@@ -942,11 +917,8 @@ __device__ void tc_apply_ts_group(TaskEnv& env, const double* Yg, long long ldy,
   // Z = Ct + Y_g^T Cb
   for (int n0 = 0; n0 < nc; n0 += 256) {
     const int nn = min(256, nc - n0), nn16 = (nn + 15) & ~15;
-    tc_gemm_tile(tc, n0, Yg, ldy, 1, wg, Cb + (size_t)n0 * ldb, ldb, 1, nn, nn16, b);
-  }
-  for (int n0 = 0; n0 < nc; n0 += 256) {
-    const int nn = min(256, nc - n0), nn16 = (nn + 15) & ~15;
-    tc_epilogue(tc, n0, nn16, [&](int r, int col, float v) {
+    tc_gemm_tile(tc, 0, Yg, ldy, 1, wg, Cb + (size_t)n0 * ldb, ldb, 1, nn, nn16, b);
+    tc_epilogue(tc, 0, nn16, [&](int r, int col, float v) {
       if (r < wg && col < nn) {
         const size_t n = n0 + col;
         Zs[r + n * 128] = v + cvt<float>(ldg(Ct + r + n * ldt));
@@ -956,11 +928,8 @@ __device__ void tc_apply_ts_group(TaskEnv& env, const double* Yg, long long ldy,
   // W = T_g^T Z; Ct -= W
   for (int n0 = 0; n0 < nc; n0 += 256) {
     const int nn = min(256, nc - n0), nn16 = (nn + 15) & ~15;
-    tc_gemm_tile(tc, n0, (const float*)Tg, 128, 1, wg, (const float*)Zs + (size_t)n0 * 128, 128, 1, nn, nn16, wg);
-  }
-  for (int n0 = 0; n0 < nc; n0 += 256) {
-    const int nn = min(256, nc - n0), nn16 = (nn + 15) & ~15;
-    tc_epilogue(tc, n0, nn16, [&](int r, int col, float v) {
+    tc_gemm_tile(tc, 0, (const float*)Tg, 128, 1, wg, (const float*)Zs + (size_t)n0 * 128, 128, 1, nn, nn16, wg);
+    tc_epilogue(tc, 0, nn16, [&](int r, int col, float v) {
       if (r < wg && col < nn) {
         const size_t n = n0 + col;
         double* p = Ct + r + n * ldt;
@@ -974,11 +943,8 @@ __device__ void tc_apply_ts_group(TaskEnv& env, const double* Yg, long long ldy,
     const int mrow = min(TC_M, b - r0);
     for (int n0 = 0; n0 < nc; n0 += 256) {
       const int nn = min(256, nc - n0), nn16 = (nn + 15) & ~15;
-      tc_gemm_tile(tc, n0, Yg + r0, 1, ldy, mrow, (const float*)Zs + (size_t)n0 * 128, 128, 1, nn, nn16, wg);
-    }
-    for (int n0 = 0; n0 < nc; n0 += 256) {
-      const int nn = min(256, nc - n0), nn16 = (nn + 15) & ~15;
-      tc_epilogue(tc, n0, nn16, [&](int r, int col, float v) {
+      tc_gemm_tile(tc, 0, Yg + r0, 1, ldy, mrow, (const float*)Zs + (size_t)n0 * 128, 128, 1, nn, nn16, wg);
+      tc_epilogue(tc, 0, nn16, [&](int r, int col, float v) {
         if (r < mrow && col < nn) {
           double* p = Cb + (r0 + r) + (size_t)(n0 + col) * ldb;
           *p = ldg(p) - cvt<double>(v);

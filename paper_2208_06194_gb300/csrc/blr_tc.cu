@@ -18,7 +18,7 @@ __global__ void __launch_bounds__(BLR_NT, 1)
   __shared__ uint32_t phase[2];
   __shared__ uint32_t tmem_base;
   __shared__ int unsafe;
-  if (threadIdx.x < 32) tmem_alloc(&tmem_base, 256);
+  if (threadIdx.x < 32) tmem_alloc(&tmem_base, 512);   // main and cross-term accumulators
   if (threadIdx.x == 0) {
     mbar_init(&bars[0], 1);
     mbar_init(&bars[1], 1);
@@ -51,7 +51,7 @@ __global__ void __launch_bounds__(BLR_NT, 1)
   }
   tc_fence_before();
   __syncthreads();
-  if (threadIdx.x < 32 && !unsafe) tmem_dealloc(tmem_base, 256);
+  if (threadIdx.x < 32 && !unsafe) tmem_dealloc(tmem_base, 512);
 }
 
 }  // namespace

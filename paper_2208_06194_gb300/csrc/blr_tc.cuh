@@ -14,6 +14,16 @@
 // Precision: every FP32 operand x is split as x = hi + lo with hi = tf32(x)
 // and lo = tf32(x - hi); the product uses hi*hi + hi*lo + lo*hi (three MMAs
 // accumulated in FP32, "3xTF32"), which keeps about FP32 accuracy.
+//
+// Accumulation.  Measured on GB300: each kind::tf32 MMA rounds its FP32
+// accumulation toward zero (a positive dot product of length K comes out
+// low by about 1.05e-8 K relative, the whole error a bias).  So the error
+// grows with the number of MMAs that feed one accumulator.  The small cross
+// terms hi*lo + lo*hi (about 2^-11 of the result) go to a second
+// accumulator TC_XCOL TMEM columns to the right, which takes two thirds of
+// the MMAs off the main one; the epilogue adds the two with round-to-nearest.
+// A product of N <= 256 columns uses TMEM columns [col0, col0 + N) and
+// [col0 + TC_XCOL, col0 + TC_XCOL + N).
 #pragma once
 #include <stdint.h>
 #include "blr_device.cuh"
@@ -21,6 +31,7 @@
 #define TC_KC 32                        // K elements per staged chunk
 #define TC_SBO (TC_KC / 4 * 128)        // bytes between 8-row groups of a chunk
 #define TC_M 128                        // rows per MMA (cta_group::1)
+#define TC_XCOL 256                     // TMEM column offset of the cross-term accumulator
 #define TC_STAGE_BYTES (2 * (2 * TC_M * TC_KC + 2 * 256 * TC_KC) * 4)   // double-buffered staging, N <= 256
 
 namespace {
@@ -259,9 +270,9 @@ __device__ bool tc_gemm_tile(TcCtx& t, uint32_t col0, const GA* A, long long sar
       for (int ks = 0; ks < TC_KC / 8; ks++) {
         const uint32_t o = ks * 256;
         const uint32_t acc = (c > 0 || ks > 0) ? 1u : 0u;
-        tc_mma(t.tmem + col0, tc_desc(a1 + o), tc_desc(b0 + o), idesc, acc);
-        tc_mma(t.tmem + col0, tc_desc(a0 + o), tc_desc(b1 + o), idesc, 1u);
-        tc_mma(t.tmem + col0, tc_desc(a0 + o), tc_desc(b0 + o), idesc, 1u);
+        tc_mma(t.tmem + col0 + TC_XCOL, tc_desc(a1 + o), tc_desc(b0 + o), idesc, acc);
+        tc_mma(t.tmem + col0 + TC_XCOL, tc_desc(a0 + o), tc_desc(b1 + o), idesc, 1u);
+        tc_mma(t.tmem + col0, tc_desc(a0 + o), tc_desc(b0 + o), idesc, acc);
       }
       tc_commit(t.bar + s);
       pend[s] = true;
@@ -421,20 +432,20 @@ __device__ bool tc_gemm_bulk(TcCtx& t, const TcBulk& q, uint32_t col0, const flo
 #pragma unroll
       for (int ks = 0; ks < TC_KC / 8; ks++) {
         const uint32_t o = ks * 256;
-        tc_mma(t.tmem + col0, tc_desc(a1 + o), tc_desc(b0 + o), idesc, (c > 0 || ks > 0) ? 1u : 0u);
-        tc_mma(t.tmem + col0, tc_desc(a0 + o), tc_desc(b1 + o), idesc, 1u);
-        tc_mma(t.tmem + col0, tc_desc(a0 + o), tc_desc(b0 + o), idesc, 1u);
+        const uint32_t acc = (c > 0 || ks > 0) ? 1u : 0u;
+        tc_mma(t.tmem + col0 + TC_XCOL, tc_desc(a1 + o), tc_desc(b0 + o), idesc, acc);
+        tc_mma(t.tmem + col0 + TC_XCOL, tc_desc(a0 + o), tc_desc(b1 + o), idesc, 1u);
+        tc_mma(t.tmem + col0, tc_desc(a0 + o), tc_desc(b0 + o), idesc, acc);
       }
       tc_commit(q.empty + s);
       empty_pend[s] = true;
-      // refill the other stage with chunk c + 1 once the MMAs of chunk c - 1
-      // (its last reader) are done; chunk c's MMAs stay queued meanwhile
-      if (c >= 1 && c + 1 < nchunk) {
-        const int o2 = s ^ 1;
-        if (!mbar_wait(q.empty + o2, q.ph[2 + o2], t.limit_ns)) { ok = false; break; }
-        q.ph[2 + o2] ^= 1u;
-        empty_pend[o2] = false;
-        load(c + 1, o2);
+      // refill this stage with chunk c + 2 once its MMAs are done (measured
+      // faster than refilling the other stage behind still-queued MMAs)
+      if (c + 2 < nchunk) {
+        if (!mbar_wait(q.empty + s, q.ph[2 + s], t.limit_ns)) { ok = false; break; }
+        q.ph[2 + s] ^= 1u;
+        empty_pend[s] = false;
+        load(c + 2, s);
       }
     }
     // drain: every commit and copy not yet waited for (normally the last one
@@ -473,8 +484,12 @@ __device__ void tc_epilogue16(const TcCtx& t, uint32_t col0, int ncol, F f) {
   const int row = quarter * 32 + lane;
   const int nblk = ncol / 16;
   for (int cb = half; cb < nblk; cb += 2) {
-    float v[16];
-    tmem_ld16(t.tmem + ((uint32_t)(quarter * 32) << 16) + col0 + cb * 16, v);
+    float v[16], x[16];
+    const uint32_t a = t.tmem + ((uint32_t)(quarter * 32) << 16) + col0 + cb * 16;
+    tmem_ld16(a, v);
+    tmem_ld16(a + TC_XCOL, x);
+#pragma unroll
+    for (int i = 0; i < 16; i++) v[i] += x[i];
     f(row, cb * 16, v);
   }
   tc_fence_before();
@@ -491,10 +506,12 @@ __device__ void tc_epilogue(const TcCtx& t, uint32_t col0, int ncol, F f) {
   const int row = quarter * 32 + lane;
   const int nblk = ncol / 16;
   for (int cb = half; cb < nblk; cb += 2) {
-    float v[16];
-    tmem_ld16(t.tmem + ((uint32_t)(quarter * 32) << 16) + col0 + cb * 16, v);
+    float v[16], x[16];
+    const uint32_t a = t.tmem + ((uint32_t)(quarter * 32) << 16) + col0 + cb * 16;
+    tmem_ld16(a, v);
+    tmem_ld16(a + TC_XCOL, x);
 #pragma unroll
-    for (int i = 0; i < 16; i++) f(row, cb * 16 + i, v[i]);
+    for (int i = 0; i < 16; i++) f(row, cb * 16 + i, v[i] + x[i]);
   }
   tc_fence_before();
   __syncthreads();

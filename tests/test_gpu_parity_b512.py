@@ -159,14 +159,14 @@ def _kappa(a):
 
 
 # (m, n, seed, tol, dense threshold, mixed): the FP64 benchmark threshold 128,
-# the mixed one 16, and 32 (more tiles cross it on the FP64 path); a ragged
-# 7 x 3 tile grid
+# the mixed one 16, and 32 (more tiles cross it on the FP64 path; at 1e-8
+# every tile of this input needs rank > 16); a ragged 7 x 3 tile grid
 WELL_CONDITIONED = [
     (4096, 2048, 71, 1e-8, 128, False),
     (4096, 2048, 71, 1e-6, 32, False),
     (3584, 1536, 73, 1e-8, 128, False),
     (4096, 2048, 71, 1e-6, 16, True),
-    (4096, 2048, 75, 1e-8, 16, True),
+    (4096, 2048, 75, 1e-8, 32, True),
     (3584, 1536, 73, 1e-6, 32, True),
 ]
 
