@@ -275,7 +275,7 @@ def tpmqrt_kinds(st, prec_is_fp64=False):
             rate = fl / cta_s / 1e9 if cta_s > 0 else 0.0
             out[name] = {"n": n, "cta_s": round(cta_s, 3), "gflop": round(fl / 1e9, 1),
                          "gflops_per_sm": round(rate, 1), "pipe": pipe,
-                         "frac_of_sm_peak": round(rate / (peak * 1e3 / 152), 4)}
+                         "frac_of_sm_peak": float(f"{rate / (peak * 1e3 / 152):.4g}")}
     return out
 
 

@@ -18,7 +18,8 @@ def _stats(total, kind_flops):
 
 
 def test_roofline_fp64_is_the_alu_peak():
-    peak = 152 * 2 * 2 * 2.07e9 / 1e12
+    peak = bench.FP64_PEAK_TFLOPS                # measured DFMA throughput
+    assert 1.0 < peak < 1.3                      # GB300: 152 SMs x 2 DFMA/clk x 2 flop x <= 2.07 GHz
     r = bench.roofline(_stats(0.5 * peak * 1e12 * 10.0, [0.0] * 8), 10.0, True)
     assert r["bound"] == "alu" and r["unit"] == "TFLOP/s"
     assert r["peak"] == pytest.approx(peak) and r["achieved"] == pytest.approx(0.5 * peak)
@@ -26,9 +27,11 @@ def test_roofline_fp64_is_the_alu_peak():
 
 
 def test_roofline_mixed_sums_tensor_and_simt_bound_times(monkeypatch):
-    monkeypatch.setattr(bench, "measured_bf16_tflops", lambda: (2250.0, "measured"))
-    p_tc = 2250.0 * 1.1 / 2.25 / 3.0            # 366.7 TFLOP/s of 3xTF32 algorithmic flops
-    p_simt = 152 * 128 * 2 * 2.07e9 / 1e12      # 80.5 TFLOP/s
+    monkeypatch.setattr(bench, "TF32_PEAK_TFLOPS", 1100.0)
+    monkeypatch.setattr(bench, "FP32_PEAK_TFLOPS", 80.0)
+    monkeypatch.setattr(bench, "TRAFFIC_FILE", "/nonexistent")
+    p_tc = 1100.0 / 3.0                         # 3xTF32: three MMAs per algorithmic product
+    p_simt = 80.0
     kinds = [1e12, 2e12, 30e12, 4e12, 5e12, 6e12, 7e12, 80e12]   # index = 4 Ydense + 2 Rdense + Adense
     total = sum(kinds) + 3e12                   # 3 TFLOP outside the updates (panels, T, ...)
     f_tc = kinds[2] + kinds[3] + kinds[5] + kinds[6] + kinds[7]
@@ -39,6 +42,7 @@ def test_roofline_mixed_sums_tensor_and_simt_bound_times(monkeypatch):
     assert r["peak"] == pytest.approx(total / t_bound / 1e12)
     assert r["achieved"] == pytest.approx(total / 2.0 / 1e12)
     assert r["tensor_part"]["tflop"] == pytest.approx(f_tc / 1e12)
+    assert r["traffic"] is None
     # the kinds that stay on SIMT (Y low-rank with R low-rank, and Y dense
     # with both R and A low-rank) are not at the tensor rate
     assert f_tc == pytest.approx(127e12)
@@ -49,7 +53,29 @@ def test_tpmqrt_kind_names():
           "tpmqrt_kind_flops": [0, 0, 2e9, 0, 0, 0, 0, 9e9]}
     out = bench.tpmqrt_kinds(st)
     assert set(out) == {"YL RD AL", "YD RD AD"}
-    assert out["YD RD AD"] == {"n": 5, "cta_s": 2.25, "gflop": 9.0}
+    d = out["YD RD AD"]
+    assert (d["n"], d["cta_s"], d["gflop"], d["pipe"]) == (5, 2.25, 9.0, "3xtf32")
+    assert d["gflops_per_sm"] == pytest.approx(4.0)
+    assert d["frac_of_sm_peak"] == pytest.approx(4.0 / (bench.TF32_PEAK_TFLOPS / 3 * 1e3 / 152), rel=1e-3)
+    assert bench.tpmqrt_kinds(st, True)["YD RD AD"]["pipe"] == "fp64"
+
+
+def test_traffic_only_for_the_captured_kernel(tmp_path, monkeypatch):
+    f = tmp_path / "cap.md"
+    f.write_text("# capture\n- csrc_sha16: " + bench.csrc_digest() + "\n- workload: small\n"
+                 "- dram_bytes_per_counted_flop: 0.01\n")
+    monkeypatch.setattr(bench, "TRAFFIC_FILE", str(f))
+    t, note = bench.dram_traffic(2e12)
+    assert t == pytest.approx(2e10) and "small" in note
+    f.write_text("- csrc_sha16: 0000000000000000\n- dram_bytes_per_counted_flop: 0.01\n")
+    assert bench.dram_traffic(2e12)[0] is None
+
+
+def test_extrapolation_uses_task_counts():
+    sample = {"mean_task_s": {"geqrt": 1.0, "larfb": 2.0, "tsqrt": 3.0, "tpmqrt": 4.0}}
+    p, q = 5, 3
+    want = 3 * 1.0 + 3 * 2.0 + (4 + 3 + 2) * 3.0 + (4 * 2 + 3 * 1 + 0) * 4.0
+    assert bench.extrapolate(sample, p, q) == pytest.approx(want)
 
 
 def _sampler_with(lines):
