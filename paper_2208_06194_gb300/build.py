@@ -25,15 +25,22 @@ def nvcc() -> str:
     return exe
 
 
-def build(verbose: bool = False) -> str:
-    """Compile every .cu file in parallel and link the shared library."""
+def build(verbose: bool = False, phase_timing: bool | None = None) -> str:
+    """Compile every .cu file in parallel and link the shared library.
+
+    phase_timing (default: the environment variable BLR_PHASE_TIMING=1)
+    compiles in the per-phase timers of the task bodies; blr_qr then prints
+    summed CTA-seconds per phase to stderr.  For profiling only."""
+    if phase_timing is None:
+        phase_timing = os.environ.get("BLR_PHASE_TIMING", "") == "1"
+    flags = FLAGS + (["-DBLR_PHASE_TIMING"] if phase_timing else [])
     os.makedirs(BUILD, exist_ok=True)
     procs = []
     objs = []
     for src in SOURCES:
         obj = os.path.join(BUILD, src.replace(".cu", ".o"))
         objs.append(obj)
-        cmd = [nvcc(), *ARCH, *FLAGS, "-c", os.path.join(CSRC, src), "-o", obj]
+        cmd = [nvcc(), *ARCH, *flags, "-c", os.path.join(CSRC, src), "-o", obj]
         if verbose:
             print(" ".join(cmd), file=sys.stderr)
         procs.append((src, subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT)))

@@ -168,8 +168,8 @@ static int plan_build(blr_factor* const* fs, int count, const blr_opts* o, blr_b
   P.fvar = (double*)(base + o_fvar);
   P.slab_peak = (unsigned long long*)(base + o_peak);
 #ifdef BLR_PHASE_TIMING
-  cudaMalloc(&P.phase, 16 * sizeof(unsigned long long));
-  cudaMemset(P.phase, 0, 16 * sizeof(unsigned long long));
+  cudaMalloc(&P.phase, 32 * sizeof(unsigned long long));
+  cudaMemset(P.phase, 0, 32 * sizeof(unsigned long long));
 #endif
   std::vector<SchedParams> mats(count, P);
   std::vector<int> mbase(count + 1), seed(count + 1);
@@ -304,10 +304,10 @@ static int plan_finish(blr_batch_plan* pl, cudaStream_t st) {
   }
 #ifdef BLR_PHASE_TIMING
   {
-    unsigned long long ph[16];
+    unsigned long long ph[32];
     cudaMemcpy(ph, P.phase, sizeof(ph), cudaMemcpyDeviceToHost);
     fprintf(stderr, "blr_qr phases (CTA-s):");
-    for (int i2 = 0; i2 < 16; i2++) fprintf(stderr, " %d:%.2f", i2, ph[i2] * 1e-9);
+    for (int i2 = 0; i2 < 32; i2++) fprintf(stderr, " %d:%.2f", i2, ph[i2] * 1e-9);
     fprintf(stderr, "\n");
   }
 #endif

@@ -100,7 +100,7 @@ struct SchedParams {
   double* fvar;                  // 8 counters: their counted flops
   float* prep;                   // mixed path: per (i,k) slot, tensor-core operands of a dense Y~_ik, or NULL
   int prep_rp;                   // rows of those operands (b rounded up to 128)
-  unsigned long long* phase;     // 16 phase-time counters (builds with BLR_PHASE_TIMING only)
+  unsigned long long* phase;     // 32 phase-time counters (builds with BLR_PHASE_TIMING only)
   unsigned long long* slab_peak; // largest scratch use of any task (doubles)
   // batches: several matrices in one launch.  Every matrix has its own copy
   // of these parameters (shape, tiles, T, DAG offsets, prepared operands)

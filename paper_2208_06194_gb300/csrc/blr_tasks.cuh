@@ -103,7 +103,8 @@ __device__ __forceinline__ float* prep_ptr(const SchedParams& P, int i, int k) {
 // TSQRT panel: Householder on [Rp (w x w upper, ld NB); Bp (ry x w, ld ldb)],
 // reflector j = [e_j; y_j] (Section 3.4.3).  Always FP64.
 // ---------------------------------------------------------------------------
-__device__ void ts_panel_qr(double* Rp, double* Bp, int ldb, int ry, int w, double* tau, Ctx& c) {
+// pos: reflectors with a non-negative beta (house_pos), used by the mixed path.
+__device__ void ts_panel_qr(double* Rp, double* Bp, int ldb, int ry, int w, double* tau, Ctx& c, bool pos) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   __syncthreads();
   for (int j = 0; j < w; j++) {
@@ -115,8 +116,10 @@ __device__ void ts_panel_qr(double* Rp, double* Bp, int ldb, int ry, int w, doub
     double sig2 = block_sum(part, c.s.red);
     if (threadIdx.x == 0) {
       double beta, tj, sc;
-      house(Rp[j + j * BLR_NB], sig2, beta, tj, sc);
+      if (pos) house_pos(Rp[j + j * BLR_NB], sig2, beta, tj, sc);
+      else house(Rp[j + j * BLR_NB], sig2, beta, tj, sc);
       flag_numeric(c, beta);
+      flag_numeric(c, tj);
       c.s.scal[0] = beta;
       c.s.scal[1] = tj;
       c.s.scal[2] = sc;
@@ -251,24 +254,28 @@ __device__ void task_geqrt(TaskEnv& env, int k, Ctx& c) {
   double* A = tile_ptr(P, k, k);
   double* Tp = t_ptr(P, k, k);
   if (std::is_same<S, double>::value) {
-    geqrf(A, b, b, b, Tp, c);
+    PH(21, geqrf(A, b, b, b, Tp, c));
     return;
   }
   double* pnl = c.s.pnl;
   for (int c0 = 0; c0 < b; c0 += BLR_NB) {
     const int w = BLR_NB, h = b - c0, ldp = h | 1;
     __syncthreads();
+    PH_BEGIN();
     stage_in(pnl, ldp, colmajor(A + c0 + (size_t)c0 * b, b), h, w);
-    panel_qr(pnl, ldp, h, w, c.s.tau, c);
+    panel_qr(pnl, ldp, h, w, c.s.tau, c, true);      // mixed path: non-negative diagonal of R
     gram_panel(pnl, ldp, h, w, c.s.z, c);
     t_recur(c.s.z, c.s.tau, w, c.s.t, c);
     for (int e = threadIdx.x; e < BLR_NB * BLR_NB; e += BLR_NT) Tp[e + (size_t)c0 * BLR_NB] = c.s.t[e];
     stage_out(colmajor(A + c0 + (size_t)c0 * b, b), pnl, ldp, h, w);
     __syncthreads();
+    PH_END(21);
     if (c0 + w < b) {
+      PH_BEGIN();
       const int ldq = stage_panel<S>(A, b, b, c0, w, Tp, c);
       apply_refl_panel(A + c0 + (size_t)(c0 + w) * b, b, h, b - c0 - w, (const S*)as<S>(c.s.pnl), ldq, w,
                        (const S*)as<S>(c.s.t), true, c);
+      PH_END(22);
     }
   }
 }
@@ -281,7 +288,7 @@ __device__ void task_larfb(TaskEnv& env, int k, int j, Ctx& c) {
   const int r = ld_rank(rank_ptr(P, k, j));
   double* C = tile_ptr(P, k, j);
   const int nc = (r < 0) ? b : r;
-  if (nc > 0) apply_q<S>(tile_ptr(P, k, k), b, b, b, t_ptr(P, k, k), C, b, nc, true, c);
+  if (nc > 0) PH(23, apply_q<S>(tile_ptr(P, k, k), b, b, b, t_ptr(P, k, k), C, b, nc, true, c));
 }
 
 
@@ -605,8 +612,9 @@ __device__ void task_tsqrt(TaskEnv& env, int i, int k, Ctx& c) {
       c.s.rp[a + l * BLR_NB] = (a <= l) ? ldg(R + (c0 + a) + (size_t)(c0 + l) * b) : 0.0;
     }
     View<double> Bp = Bv.shifted(0, c0);
-    stage_in(c.s.pnl, ldb, Bp, ry, w);
-    ts_panel_qr(c.s.rp, c.s.pnl, ldb, ry, w, c.s.tau, c);
+    PH(16, stage_in(c.s.pnl, ldb, Bp, ry, w));
+    PH(17, ts_panel_qr(c.s.rp, c.s.pnl, ldb, ry, w, c.s.tau, c, std::is_same<S, float>::value));
+    PH_BEGIN();
     gram_dense(c.s.pnl, ldb, ry, w, c.s.z, c);
     t_recur(c.s.z, c.s.tau, w, c.s.t, c);
     for (int e = threadIdx.x; e < BLR_NB * BLR_NB; e += BLR_NT) Tk[e + (size_t)c0 * BLR_NB] = c.s.t[e];
@@ -616,7 +624,9 @@ __device__ void task_tsqrt(TaskEnv& env, int i, int k, Ctx& c) {
     }
     stage_out(Bp, c.s.pnl, ldb, ry, w);
     __syncthreads();
+    PH_END(18);
     if (c0 + w < gend) {
+      PH_BEGIN();
       View<double> Cb = Bv.shifted(0, c0 + w);
       if (std::is_same<S, double>::value) {
         apply_refl_ts(R + c0 + (size_t)(c0 + w) * b, b, Cb, ry, gend - c0 - w, c.s.pnl, ldb, w, c.s.t, true, c);
@@ -625,12 +635,13 @@ __device__ void task_tsqrt(TaskEnv& env, int i, int k, Ctx& c) {
         apply_refl_ts(R + c0 + (size_t)(c0 + w) * b, b, Cb, ry, gend - c0 - w, (const S*)as<S>(c.s.pnl), ldy, w,
                       (const S*)as<S>(c.s.t), true, c);
       }
+      PH_END(19);
     }
     __syncthreads();
     if (grouped && c0 + w == gend && gend < b) {
       const int g0 = gend - 128;
-      tc_apply_ts_group(env, B + (size_t)g0 * b, b, 128, Tk + (size_t)g0 * BLR_NB, R + g0 + (size_t)gend * b, b,
-                        B + (size_t)gend * b, b, b - gend, gTg, gZs, c);
+      PH(20, tc_apply_ts_group(env, B + (size_t)g0 * b, b, 128, Tk + (size_t)g0 * BLR_NB, R + g0 + (size_t)gend * b,
+                               b, B + (size_t)gend * b, b, b - gend, gTg, gZs, c));
     }
   }
   if constexpr (std::is_same<S, float>::value) {
