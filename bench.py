@@ -357,7 +357,7 @@ def cpu_baseline(pr_args, tol, dense_rank):
     O.blr_qr(a1, 1e-14)
     cfg1 = time.perf_counter() - t0
     cores = _host_cores()
-    return {"value": est, "unit": "s", "cores": cores, "kind": "oracle_extrapolated",
+    return {"value": est, "unit": "s", "cores": cores, "kind": "oracle", "method": "extrapolated",
             "threads": os.environ.get("OMP_NUM_THREADS", f"numpy BLAS default ({cores} host cores)"),
             "sample": (f"oracle Algorithm 4 timed in full on {mid['workload']} ({mid['seconds']:.1f} s, "
                        f"{sum(mid['tasks'].values())} tasks); its mean time per task type x the task counts "
@@ -392,7 +392,7 @@ def run_reference(args, rank, world):
             "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
             "config": {"workload": workload_name(args), "global_batch": 1, "dense_rank": args.dense_rank},
-            "cpu_baseline": {"kind": "oracle_extrapolated", "cores": cores, "value": v, "unit": "s",
+            "cpu_baseline": {"kind": "oracle", "method": "extrapolated", "cores": cores, "value": v, "unit": "s",
                              "sample": (f"per step: oracle Algorithm 4 timed in full on {last['workload']} "
                                         f"({last['seconds']:.1f} s); mean time per task type x the task counts of "
                                         f"the {s['m']}x{s['n']} factorization")},

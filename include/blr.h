@@ -88,6 +88,15 @@ typedef struct blr_batch_plan blr_batch_plan; /* opaque launch plan for one or s
  *               never released, so the scheduler stalls and the watchdog
  *               ends the call with BLR_ERR_TIMEOUT.  Only a device wait that
  *               runs out: nothing faults.
+ *  prep_slots   mixed path: slots in the pool of prepared tensor-core
+ *               operands (6 x b_r x b floats each, b_r = b rounded up to 128:
+ *               6 MB at b = 512).  An update QR takes a free slot for its
+ *               reflector block and the slot returns to the pool when the
+ *               last update of that block has used it; a block that finds no
+ *               free slot is applied from its stored factors instead (same
+ *               result, slower).  0 = automatic: one slot per reflector
+ *               block when the device has room, else as many as fit while
+ *               4 GB stay free.
  */
 typedef struct blr_opts {
   int b;
@@ -102,7 +111,8 @@ typedef struct blr_opts {
   int trace;
   double eta;
   int test_withhold;
-  int reserved[3];
+  int prep_slots;
+  int reserved[2];
 } blr_opts;
 
 /* One task of a traced factorization (blr_trace_export). */
@@ -136,6 +146,8 @@ typedef struct blr_stats_t {
   double tpmqrt_kind_flops[8];   /* factor only: their counted FP ops */
   long long scratch_peak_bytes;  /* factor only: largest per-CTA scratch use of any task */
   long long scratch_bytes;       /* factor only: per-CTA scratch slabs allocated (all CTAs) */
+  long long prep_slots;          /* factor only, mixed path: slots in the prepared-operand pool */
+  long long prep_misses;         /* factor only, mixed path: reflector blocks that found no free slot */
 } blr_stats_t;
 
 /* Fills *opts with the defaults (b = 512, tol = 1e-8, FP64). */

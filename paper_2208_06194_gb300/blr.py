@@ -34,7 +34,8 @@ class Opts(ctypes.Structure):
                 ("rec_tol", ctypes.c_double), ("dense_rank", ctypes.c_int),
                 ("precision", ctypes.c_int), ("sched_ctas", ctypes.c_int),
                 ("watchdog_ms", ctypes.c_int), ("scratch_b2", ctypes.c_int), ("trace", ctypes.c_int),
-                ("eta", ctypes.c_double), ("test_withhold", ctypes.c_int), ("reserved", ctypes.c_int * 3)]
+                ("eta", ctypes.c_double), ("test_withhold", ctypes.c_int), ("prep_slots", ctypes.c_int),
+                ("reserved", ctypes.c_int * 2)]
 
 
 class TraceEvent(ctypes.Structure):
@@ -51,7 +52,8 @@ class Stats(ctypes.Structure):
                 ("task_seconds", ctypes.c_double * 4), ("seconds", ctypes.c_double),
                 ("tpmqrt_kind", ctypes.c_longlong * 8), ("tpmqrt_kind_seconds", ctypes.c_double * 8),
                 ("tpmqrt_kind_flops", ctypes.c_double * 8), ("scratch_peak_bytes", ctypes.c_longlong),
-                ("scratch_bytes", ctypes.c_longlong)]
+                ("scratch_bytes", ctypes.c_longlong), ("prep_slots", ctypes.c_longlong),
+                ("prep_misses", ctypes.c_longlong)]
 
 
 _lib = None

@@ -271,8 +271,8 @@ extern "C" int blr_matrix_clone(const blr_matrix* a, blr_matrix** out, void* str
 
 int blr_check_qr_opts(const blr_opts* opts) {
   if (!opts) { blr_set_error("opts is NULL"); return BLR_ERR_INVALID; }
-  if (opts->trace < 0 || opts->test_withhold < 0) {
-    blr_set_error("negative trace or test_withhold option");
+  if (opts->trace < 0 || opts->test_withhold < 0 || opts->prep_slots < 0) {
+    blr_set_error("negative trace, test_withhold or prep_slots option");
     return BLR_ERR_INVALID;
   }
   if (opts->rec_tol < 0 || (opts->rec_tol == 0 && opts->tol <= 0)) {
@@ -383,6 +383,8 @@ extern "C" int blr_stats(const void* handle, int handle_is_factor, blr_stats_t* 
     out->seconds = f->seconds;
     out->scratch_peak_bytes = f->scratch_peak_bytes;
     out->scratch_bytes = f->scratch_bytes;
+    out->prep_slots = f->prep_slots;
+    out->prep_misses = f->prep_misses;
     for (int v = 0; v < 8; v++) {
       out->tpmqrt_kind[v] = f->tpmqrt_kind[v];
       out->tpmqrt_kind_seconds[v] = f->tpmqrt_kind_seconds[v];

@@ -148,28 +148,6 @@ __device__ __forceinline__ void house(S alpha, S sig2, S& beta, S& tau, S& scale
   scale = S(1) / (alpha - beta);
 }
 
-// The reflector with a non-negative beta: H x = beta e_1, beta = +||x||
-// (Golub & Van Loan's choice), v_1 = alpha - beta computed without
-// cancellation as -sig2 / (alpha + beta) when alpha > 0.  For a column whose
-// tail is small against alpha > 0 the reflector is close to the identity
-// (tau ~ sig2 / (2 alpha^2)) instead of the sign flip of the choice above
-// (tau ~ 2); the mixed-precision path uses it for its panels so that the
-// FP32-class updates of an update-QR chain stay small against R.
-template <class S>
-__device__ __forceinline__ void house_pos(S alpha, S sig2, S& beta, S& tau, S& scale) {
-  if (sig2 == S(0) && alpha >= S(0)) {
-    beta = alpha;
-    tau = S(0);
-    scale = S(0);
-    return;
-  }
-  const S nrm = sqrt(alpha * alpha + sig2);
-  const S v1 = (alpha > S(0)) ? -sig2 / (alpha + nrm) : alpha - nrm;
-  beta = nrm;
-  tau = -v1 / nrm;
-  scale = S(1) / v1;
-}
-
 __device__ __forceinline__ void flag_numeric(Ctx& c, double x) {
   if (!isfinite(x)) atomicOr(c.status, ST_NUMERIC);
 }
@@ -270,9 +248,8 @@ __device__ void zero_mat(D* dst, long long ldd, int rows, int cols) {
 // Unblocked Householder QR of a panel held in shared memory (h x w, w <= 32):
 // R in the upper triangle, v_j below the diagonal, tau[j].
 // ---------------------------------------------------------------------------
-// pos: reflectors with a non-negative beta (house_pos) instead of house.
 template <class S>
-__device__ void panel_qr(S* P, int ldp, int h, int w, S* tau, Ctx& c, bool pos = false) {
+__device__ void panel_qr(S* P, int ldp, int h, int w, S* tau, Ctx& c) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   S* scal = as<S>(c.s.scal);
   __syncthreads();
@@ -285,8 +262,7 @@ __device__ void panel_qr(S* P, int ldp, int h, int w, S* tau, Ctx& c, bool pos =
     S sig2 = block_sum(part, c.s.red);
     if (threadIdx.x == 0) {
       S beta, tj, sc;
-      if (pos) house_pos(P[j + j * ldp], sig2, beta, tj, sc);
-      else house(P[j + j * ldp], sig2, beta, tj, sc);
+      house(P[j + j * ldp], sig2, beta, tj, sc);
       flag_numeric(c, (double)beta);
       flag_numeric(c, (double)tj);
       scal[0] = beta;

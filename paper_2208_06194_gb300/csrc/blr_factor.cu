@@ -29,7 +29,11 @@ struct blr_batch_plan {
   int* deps0 = nullptr;                   // device: initial dependency counters
   int* seed = nullptr;                    // device: the count initially ready tasks, then count
   double* scratch = nullptr;
-  float* prep = nullptr;
+  float* prep = nullptr;                  // pool of prepared tensor-core operands (mixed path)
+  int* prep_state = nullptr;              // pool state: per-slot counters, search start, misses, then slot_of
+  size_t prep_state_zero = 0;             // bytes of prep_state reset to 0 per launch (the rest to -1)
+  size_t prep_state_bytes = 0;
+  int nslot = 0;
   blr_trace_event* trace = nullptr;       // opts.trace events (device)
   SchedParams P{};
   int ctas = 0, n_tasks = 0;
@@ -43,6 +47,7 @@ static void plan_free(blr_batch_plan* pl) {
   if (pl->e1) cudaEventDestroy(pl->e1);
   if (pl->scratch) cudaFree(pl->scratch);
   if (pl->prep) cudaFree(pl->prep);
+  if (pl->prep_state) cudaFree(pl->prep_state);
   if (pl->trace) cudaFree(pl->trace);
   if (pl->base) cudaFree(pl->base);
 #ifdef BLR_PHASE_TIMING
@@ -63,12 +68,12 @@ static int plan_build(blr_factor* const* fs, int count, const blr_opts* o, blr_b
     int p, q, b, nt;
     std::vector<int> offL, offS, offP;
     std::vector<long long> toff;
-    size_t o_offL, o_offS, o_offP, o_toff, prep_off;
+    size_t o_offL, o_offS, o_offP, o_toff, slot_of_off;
     int base;
   };
   std::vector<Mat> M(count);
   int total = 0, bmax = 0;
-  size_t prep_floats = 0;
+  size_t slot_floats = 0, nt_total = 0;
   for (int m = 0; m < count; m++) {
     const blr_matrix& A = fs[m]->a;
     Mat& x = M[m];
@@ -80,8 +85,9 @@ static int plan_build(blr_factor* const* fs, int count, const blr_opts* o, blr_b
     long long acc = 0;
     for (int k = 0; k < x.q; k++) { x.toff[k] = acc; acc += x.p - k; }
     bmax = std::max(bmax, x.b);
-    x.prep_off = prep_floats;
-    prep_floats += (size_t)x.nt * 6 * ((x.b + 127) / 128 * 128) * x.b;
+    x.slot_of_off = nt_total;
+    nt_total += (size_t)x.nt;
+    slot_floats = std::max(slot_floats, (size_t)6 * ((x.b + 127) / 128 * 128) * x.b);
   }
   pl->n_tasks = total;
   std::vector<int> deps(total);
@@ -129,12 +135,35 @@ static int plan_build(blr_factor* const* fs, int count, const blr_opts* o, blr_b
     blr_set_error("blr_qr: out of device memory (scratch %zu MB)", mb);
     return BLR_ERR_OOM;
   }
-  // mixed path: tensor-core operands of every dense reflector block (one slot
-  // per (i,k), i >= k); if the device cannot hold them the updates stage
-  // their operands themselves
-  if (o->precision == BLR_PREC_MIXED && cudaMalloc(&pl->prep, sizeof(float) * prep_floats) != cudaSuccess) {
-    pl->prep = nullptr;
-    cudaGetLastError();
+  // mixed path: a pool of slots for the tensor-core operands of reflector
+  // blocks, one per block when the device has room (or opts.prep_slots); a
+  // block that finds no free slot is applied from its stored factors
+  if (o->precision == BLR_PREC_MIXED) {
+    size_t want = nt_total;
+    if (o->prep_slots > 0) {
+      want = std::min(want, (size_t)o->prep_slots);
+    } else {
+      size_t fr = 0, tot = 0;
+      const size_t reserve = (size_t)4 << 30;
+      if (cudaMemGetInfo(&fr, &tot) == cudaSuccess)
+        want = std::min(want, fr > reserve ? (fr - reserve) / (slot_floats * sizeof(float)) : (size_t)0);
+      cudaGetLastError();
+    }
+    while (want > 0 && cudaMalloc(&pl->prep, sizeof(float) * slot_floats * want) != cudaSuccess) {
+      pl->prep = nullptr;
+      cudaGetLastError();
+      want /= 2;
+    }
+    pl->nslot = pl->prep ? (int)want : 0;
+    if (pl->prep) {
+      pl->prep_state_zero = (sizeof(int) * want + sizeof(unsigned long long) * 2 + 255) & ~(size_t)255;
+      pl->prep_state_bytes = pl->prep_state_zero + sizeof(int) * nt_total;
+      if (cudaMalloc(&pl->prep_state, pl->prep_state_bytes) != cudaSuccess) {
+        plan_free(pl);
+        blr_set_error("blr_qr: out of device memory (prepared-operand pool state)");
+        return BLR_ERR_OOM;
+      }
+    }
   }
   if (o->trace > 0 && cudaMalloc(&pl->trace, sizeof(blr_trace_event) * (size_t)o->trace) != cudaSuccess) {
     plan_free(pl);
@@ -184,8 +213,18 @@ static int plan_build(blr_factor* const* fs, int count, const blr_opts* o, blr_b
     Q.off_larfb = (const int*)(base + M[m].o_offL);
     Q.off_tsqrt = (const int*)(base + M[m].o_offS);
     Q.off_tpmqrt = (const int*)(base + M[m].o_offP);
-    Q.prep = pl->prep ? pl->prep + M[m].prep_off : nullptr;
+    Q.prep = pl->prep;
     Q.prep_rp = (A.b + 127) / 128 * 128;
+    Q.prep_nslot = pl->nslot;
+    Q.prep_slot_floats = slot_floats;
+    if (pl->prep) {
+      char* ps = reinterpret_cast<char*>(pl->prep_state);
+      Q.prep_ref = reinterpret_cast<int*>(ps);
+      Q.prep_next = reinterpret_cast<unsigned int*>(ps + sizeof(int) * pl->nslot);
+      Q.prep_miss = reinterpret_cast<unsigned long long*>(
+          ps + ((sizeof(int) * pl->nslot + sizeof(unsigned int) + 7) & ~(size_t)7));
+      Q.prep_slot_of = reinterpret_cast<int*>(ps + pl->prep_state_zero) + M[m].slot_of_off;
+    }
     Q.task_base = M[m].base;
     Q.mat_index = m;
     mbase[m] = M[m].base;
@@ -239,6 +278,12 @@ static int plan_launch(blr_batch_plan* pl, cudaStream_t st) {
   }
   SchedParams& P = pl->P;
   if (!rc) rc = blr_cuda_check(cudaMemsetAsync(pl->base + pl->dyn_off, 0, pl->dyn_bytes, st), "reset scheduler");
+  if (!rc && pl->prep_state) {
+    rc = blr_cuda_check(cudaMemsetAsync(pl->prep_state, 0, pl->prep_state_zero, st), "reset operand pool");
+    if (!rc)
+      rc = blr_cuda_check(cudaMemsetAsync(reinterpret_cast<char*>(pl->prep_state) + pl->prep_state_zero, 0xff,
+                                          pl->prep_state_bytes - pl->prep_state_zero, st), "reset operand slots");
+  }
   if (!rc) rc = blr_cuda_check(cudaMemcpyAsync(P.deps, pl->deps0, sizeof(int) * pl->n_tasks, cudaMemcpyDeviceToDevice, st), "reset deps");
   if (!rc) rc = blr_cuda_check(cudaMemsetAsync(P.qbuf, 0xff, sizeof(int) * (size_t)BLR_NQ * pl->n_tasks, st), "reset queues");
   if (!rc) rc = blr_cuda_check(cudaMemcpyAsync(P.qbuf, pl->seed, sizeof(int) * pl->count, cudaMemcpyDeviceToDevice, st), "seed queue");
@@ -272,6 +317,8 @@ static int plan_finish(blr_batch_plan* pl, cudaStream_t st) {
   cudaMemcpy(tv, P.tvar, sizeof(tv), cudaMemcpyDeviceToHost);
   cudaMemcpy(fv, P.fvar, sizeof(fv), cudaMemcpyDeviceToHost);
   cudaMemcpy(&peak, P.slab_peak, sizeof(peak), cudaMemcpyDeviceToHost);
+  unsigned long long misses = 0;
+  if (P.prep) cudaMemcpy(&misses, P.prep_miss, sizeof(misses), cudaMemcpyDeviceToHost);
   unsigned int tn = 0;
   std::vector<blr_trace_event> trace;
   if (P.trace) {
@@ -286,6 +333,8 @@ static int plan_finish(blr_batch_plan* pl, cudaStream_t st) {
   for (blr_factor* f : pl->fac) {
     f->trace = trace;
     f->trace_total = tn;
+    f->prep_slots = pl->nslot;
+    f->prep_misses = (long long)misses;
     f->seconds = ms * 1e-3;
     f->scratch_peak_bytes = (long long)(peak * sizeof(double));
     f->scratch_bytes = (long long)(sizeof(double) * pl->slab * pl->ctas);

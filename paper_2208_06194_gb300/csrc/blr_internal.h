@@ -65,6 +65,8 @@ struct blr_factor {
   double tpmqrt_kind_flops[8];
   long long scratch_peak_bytes;
   long long scratch_bytes;
+  long long prep_slots;
+  long long prep_misses;
   double seconds;
   std::vector<blr_trace_event> trace;   // host copy of the launch's task trace (opts.trace > 0)
   long long trace_total;                // tasks the traced launch ran
@@ -98,8 +100,18 @@ struct SchedParams {
   unsigned long long* nvar;      // 8 counters: updates per operand kind (4 Y dense + 2 R dense + A dense)
   unsigned long long* tvar;      // 8 counters: their summed durations (ns)
   double* fvar;                  // 8 counters: their counted flops
-  float* prep;                   // mixed path: per (i,k) slot, tensor-core operands of a dense Y~_ik, or NULL
-  int prep_rp;                   // rows of those operands (b rounded up to 128)
+  // mixed path: a pool of slots of prepared tensor-core operands, shared by
+  // every matrix of a launch.  An update QR (i,k) takes a free slot and
+  // records it in prep_slot_of[toff[k] + i - k]; prep_ref counts the updates
+  // still to use it (0 free, -1 being prepared); the last one frees it.
+  float* prep;                   // pool base, or NULL
+  int prep_rp;                   // rows of the operands (this matrix's b rounded up to 128)
+  int prep_nslot;                // slots in the pool
+  size_t prep_slot_floats;       // floats per slot (the largest matrix of the launch)
+  int* prep_slot_of;             // this matrix's reflector blocks: slot or -1
+  int* prep_ref;                 // per slot
+  unsigned int* prep_next;       // rotating start of the free-slot search
+  unsigned long long* prep_miss; // blocks that found no free slot
   unsigned long long* phase;     // 32 phase-time counters (builds with BLR_PHASE_TIMING only)
   unsigned long long* slab_peak; // largest scratch use of any task (doubles)
   // batches: several matrices in one launch.  Every matrix has its own copy

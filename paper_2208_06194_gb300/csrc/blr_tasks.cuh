@@ -94,17 +94,32 @@ __device__ void release_task(const SchedParams& P, const DagShape& d, int sid) {
   }
 }
 
-// Slot of the tensor-core operands prepared for the reflector block (i,k).
-__device__ __forceinline__ float* prep_ptr(const SchedParams& P, int i, int k) {
-  return P.prep + (size_t)(P.toff_dev[k] + (i - k)) * 6 * P.prep_rp * P.b;
+// The pool of prepared tensor-core operands (mixed path).  Reflector block
+// (i,k) has index toff[k] + i - k in prep_slot_of; a slot is
+// prep_slot_floats floats.
+__device__ __forceinline__ int prep_block(const SchedParams& P, int i, int k) {
+  return (int)(P.toff_dev[k] + (i - k));
+}
+__device__ __forceinline__ float* prep_at(const SchedParams& P, int slot) {
+  return P.prep + (size_t)slot * P.prep_slot_floats;
+}
+// Thread 0: a free slot, marked as being prepared (-1), or -1 when a bounded
+// search finds none (the block's updates then use its stored factors).
+__device__ int prep_acquire(const SchedParams& P) {
+  const int tries = P.prep_nslot < 64 ? P.prep_nslot : 64;
+  for (int a = 0; a < tries; a++) {
+    const int s = (int)(atomicAdd(P.prep_next, 1u) % (unsigned)P.prep_nslot);
+    if (atomicCAS(P.prep_ref + s, 0, -1) == 0) return s;
+  }
+  atomicAdd(P.prep_miss, 1ull);
+  return -1;
 }
 
 // ---------------------------------------------------------------------------
 // TSQRT panel: Householder on [Rp (w x w upper, ld NB); Bp (ry x w, ld ldb)],
 // reflector j = [e_j; y_j] (Section 3.4.3).  Always FP64.
 // ---------------------------------------------------------------------------
-// pos: reflectors with a non-negative beta (house_pos), used by the mixed path.
-__device__ void ts_panel_qr(double* Rp, double* Bp, int ldb, int ry, int w, double* tau, Ctx& c, bool pos) {
+__device__ void ts_panel_qr(double* Rp, double* Bp, int ldb, int ry, int w, double* tau, Ctx& c) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   __syncthreads();
   for (int j = 0; j < w; j++) {
@@ -116,8 +131,7 @@ __device__ void ts_panel_qr(double* Rp, double* Bp, int ldb, int ry, int w, doub
     double sig2 = block_sum(part, c.s.red);
     if (threadIdx.x == 0) {
       double beta, tj, sc;
-      if (pos) house_pos(Rp[j + j * BLR_NB], sig2, beta, tj, sc);
-      else house(Rp[j + j * BLR_NB], sig2, beta, tj, sc);
+      house(Rp[j + j * BLR_NB], sig2, beta, tj, sc);
       flag_numeric(c, beta);
       flag_numeric(c, tj);
       c.s.scal[0] = beta;
@@ -246,6 +260,11 @@ __device__ void recompress_side(TaskEnv& env, S* Uf, int ldu, const S* H, const 
 // Panel factorizations (Householder norms, tau, vectors, T) are FP64 on both.
 // ---------------------------------------------------------------------------
 
+__device__ void tc_apply_explicit_group(TaskEnv& env, const double* Yg, long long ldy, int h, int wg,
+                                        const double* Tblk, double* C, long long ldc, int nc, float* Tg, float* Zs,
+                                        Ctx& c);
+__device__ void explicit_reflectors(const double* A, int b, int g0, int wg, double* Yx);
+
 // GEQRT(k): Householder QR of the dense diagonal tile (Section 3.4.1).
 template <class S>
 __device__ void task_geqrt(TaskEnv& env, int k, Ctx& c) {
@@ -258,24 +277,45 @@ __device__ void task_geqrt(TaskEnv& env, int k, Ctx& c) {
     return;
   }
   double* pnl = c.s.pnl;
+  // the panels' updates reach only the columns of their 128-column group;
+  // each finished group updates the columns to its right on the tensor
+  // cores (tc_apply_explicit_group)
+  const bool grouped = env.tc != nullptr && b > 128;
+  float *gTg = nullptr, *gZs = nullptr;
+  double* gY = nullptr;
+  if (grouped) {
+    gTg = (float*)env.alloc(128 * 128 / 2);
+    gZs = (float*)env.alloc((size_t)128 * b / 2);
+    gY = env.alloc((size_t)128 * b);
+  }
   for (int c0 = 0; c0 < b; c0 += BLR_NB) {
     const int w = BLR_NB, h = b - c0, ldp = h | 1;
+    const int gend = grouped ? min(b, (c0 / 128 + 1) * 128) : b;   // end of this panel's update range
     __syncthreads();
     PH_BEGIN();
     stage_in(pnl, ldp, colmajor(A + c0 + (size_t)c0 * b, b), h, w);
-    panel_qr(pnl, ldp, h, w, c.s.tau, c, true);      // mixed path: non-negative diagonal of R
+    panel_qr(pnl, ldp, h, w, c.s.tau, c);
     gram_panel(pnl, ldp, h, w, c.s.z, c);
     t_recur(c.s.z, c.s.tau, w, c.s.t, c);
     for (int e = threadIdx.x; e < BLR_NB * BLR_NB; e += BLR_NT) Tp[e + (size_t)c0 * BLR_NB] = c.s.t[e];
     stage_out(colmajor(A + c0 + (size_t)c0 * b, b), pnl, ldp, h, w);
     __syncthreads();
     PH_END(21);
-    if (c0 + w < b) {
+    if (c0 + w < gend) {
       PH_BEGIN();
       const int ldq = stage_panel<S>(A, b, b, c0, w, Tp, c);
-      apply_refl_panel(A + c0 + (size_t)(c0 + w) * b, b, h, b - c0 - w, (const S*)as<S>(c.s.pnl), ldq, w,
+      apply_refl_panel(A + c0 + (size_t)(c0 + w) * b, b, h, gend - c0 - w, (const S*)as<S>(c.s.pnl), ldq, w,
                        (const S*)as<S>(c.s.t), true, c);
       PH_END(22);
+    }
+    __syncthreads();
+    if (grouped && c0 + w == gend && gend < b) {
+      const int g0 = gend - 128;
+      PH_BEGIN();
+      explicit_reflectors(A, b, g0, 128, gY);
+      tc_apply_explicit_group(env, gY, b - g0, b - g0, 128, Tp + (size_t)g0 * BLR_NB, A + g0 + (size_t)gend * b, b,
+                              b - gend, gTg, gZs, c);
+      PH_END(28);
     }
   }
 }
@@ -288,6 +328,25 @@ __device__ void task_larfb(TaskEnv& env, int k, int j, Ctx& c) {
   const int r = ld_rank(rank_ptr(P, k, j));
   double* C = tile_ptr(P, k, j);
   const int nc = (r < 0) ? b : r;
+  if constexpr (std::is_same<S, float>::value) {
+    if (r < 0 && env.tc && b > 128) {
+      // a dense tile on the mixed path: Q_kk^T C one group of 128 reflectors
+      // at a time on the tensor cores (rows g0 .. b of C)
+      PH_BEGIN();
+      float* gTg = (float*)env.alloc(128 * 128 / 2);
+      float* gZs = (float*)env.alloc((size_t)128 * b / 2);
+      double* gY = env.alloc((size_t)128 * b);
+      const double* A = tile_ptr(P, k, k);
+      const double* Tp = t_ptr(P, k, k);
+      for (int g0 = 0; g0 < b; g0 += 128) {
+        const int wg = min(128, b - g0);
+        explicit_reflectors(A, b, g0, wg, gY);
+        tc_apply_explicit_group(env, gY, b - g0, b - g0, wg, Tp + (size_t)g0 * BLR_NB, C + g0, b, b, gTg, gZs, c);
+      }
+      PH_END(23);
+      return;
+    }
+  }
   if (nc > 0) PH(23, apply_q<S>(tile_ptr(P, k, k), b, b, b, t_ptr(P, k, k), C, b, nc, true, c));
 }
 
@@ -304,12 +363,11 @@ __device__ void task_larfb(TaskEnv& env, int k, int j, Ctx& c) {
 // Gram matrix G = Y^T Y of the tails (the identity parts are orthogonal):
 // T(0:J, J) = -T(0:J, 0:J) G(0:J, J) T_J, one 32-column block J at a time.
 // ---------------------------------------------------------------------------
-__device__ void tsqrt_prep(TaskEnv& env, int i, int k, Ctx& c) {
+__device__ void tsqrt_prep(TaskEnv& env, int i, int k, float* slot, Ctx& c) {
   const SchedParams& P = *env.P;
   TcCtx& tc = *env.tc;
   const int b = P.b, Rp = P.prep_rp;
   const size_t op = (size_t)Rp * b;
-  float* slot = prep_ptr(P, i, k);
   float *yt_h = slot, *yt_l = slot + op, *yc_h = slot + 2 * op, *yc_l = slot + 3 * op, *tt_h = slot + 4 * op,
         *tt_l = slot + 5 * op;
   const int r = ld_rank(rank_ptr(P, i, k));
@@ -317,6 +375,7 @@ __device__ void tsqrt_prep(TaskEnv& env, int i, int k, Ctx& c) {
   // the tails: dense Y (b x b) in the tile, or a low-rank tile's Y (r x b)
   // stored transposed in its V slot; Kt = tail length rounded up to a chunk
   const int Kt = r < 0 ? b : (r + TC_KC - 1) / TC_KC * TC_KC;
+  PH_BEGIN();
   if (r < 0) {
     const double* Y = tile_ptr(P, i, k);
     tc_canon(yt_h, yt_l, Rp, b, Y, b, 1, b, b);      // (a, s) = Y[s + a b]
@@ -329,6 +388,8 @@ __device__ void tsqrt_prep(TaskEnv& env, int i, int k, Ctx& c) {
   }
   fence_async_global();
   __syncthreads();
+  PH_END(24);
+  PH_BEGIN();
   // G = Y^T Y (FP32, ld b, upper block triangle)
   float* G = (float*)env.alloc((size_t)b * b / 2);
   float* T = (float*)env.alloc((size_t)b * b / 2);
@@ -345,40 +406,36 @@ __device__ void tsqrt_prep(TaskEnv& env, int i, int k, Ctx& c) {
     }
   }
   c.fma += (double)b * b * Kt / 2;
-  // T, block column by block column (X = G(0:J, J) T_J in shared memory)
+  PH_END(25);
+  // T from its 32 x 32 diagonal blocks by merging neighbouring blocks of
+  // h reflectors into blocks of 2h: for the product of the compact WY forms
+  // (I - Y1 T1 Y1^T)(I - Y2 T2 Y2^T) = I - [Y1 Y2] T [Y1 Y2]^T the new
+  // off-diagonal block is T12 = -T1 (Y1^T Y2) T2 = -T1 G12 T2 (Eq. 3 for a
+  // block of reflectors, the Schreiber-Van Loan recurrence taken a block at
+  // a time); each merge is two FP32 products in shared-memory tiles.
+  PH_BEGIN();
   for (int e = threadIdx.x; e < b * b; e += BLR_NT) {
     const int a = e % b, l = e / b;
     T[e] = ((a >> 5) == (l >> 5) && a <= l) ? cvt<float>(ldg(Tk + (size_t)l * BLR_NB + (a & 31))) : 0.f;
   }
   __syncthreads();
-  float* X = tc.buf;                      // top x 32, ld b (the staging area is idle here)
-  for (int J = 1; J * BLR_NB < b; J++) {
-    const int top = J * BLR_NB;
-    for (int e = threadIdx.x; e < top * BLR_NB; e += BLR_NT) {
-      const int a = e % top, m = e / top;
-      float s = 0.f;
-      for (int l = 0; l <= m; l++) s += __ldcg(G + a + (size_t)(top + l) * b) * __ldcg(T + (top + l) + (size_t)(top + m) * b);
-      X[a + m * b] = s;
+  float* X = (float*)env.alloc((size_t)b * b / 4);         // b/2 x b/2 products G12 T2 (ld b/2)
+  const int ldx = b / 2;
+  for (int h = BLR_NB; h < b; h *= 2) {
+    for (int j0 = 0; j0 + h < b; j0 += 2 * h) {
+      const int h2 = min(h, b - j0 - h);
+      // X = G(j0:j0+h, j0+h:j0+h+h2) T(j0+h:j0+h+h2, j0+h:j0+h+h2)
+      gemm(h, h2, h2, 1.f, G + j0 + (size_t)(j0 + h) * b, b, false, (const float*)T + (j0 + h) + (size_t)(j0 + h) * b,
+           b, false, 0.f, X, ldx, c);
+      __syncthreads();
+      // T(j0:j0+h, j0+h:j0+h+h2) = -T(j0:j0+h, j0:j0+h) X
+      gemm(h, h2, h, -1.f, (const float*)T + j0 + (size_t)j0 * b, b, false, (const float*)X, ldx, false, 0.f,
+           T + j0 + (size_t)(j0 + h) * b, b, c);
+      __syncthreads();
     }
-    __syncthreads();
-    // T(0:top, J) = -T(0:top, 0:top) X: thread = (row a, 8 columns)
-    for (int e = threadIdx.x; e < top * 4; e += BLR_NT) {
-      const int a = e % top, m0 = (e / top) * 8;
-      float s[8];
-#pragma unroll
-      for (int u = 0; u < 8; u++) s[u] = 0.f;
-      for (int l = a; l < top; l++) {
-        const float t = __ldcg(T + a + (size_t)l * b);
-#pragma unroll
-        for (int u = 0; u < 8; u++) s[u] += t * X[l + (m0 + u) * b];
-      }
-#pragma unroll
-      for (int u = 0; u < 8; u++) T[a + (size_t)(top + m0 + u) * b] = -s[u];
-    }
-    __syncthreads();
-    c.fma += (double)top * BLR_NB * BLR_NB / 2 + (double)top * top * BLR_NB / 2;
   }
-  tc_canon(tt_h, tt_l, Rp, b, (const float*)T, b, 1, b, b);   // (a, k) = T(k, a) = T[k + a b]
+  PH_END(26);
+  PH(27, tc_canon(tt_h, tt_l, Rp, b, (const float*)T, b, 1, b, b));   // (a, k) = T(k, a) = T[k + a b]
   fence_async_global();
   __threadfence();
   __syncthreads();
@@ -613,7 +670,7 @@ __device__ void task_tsqrt(TaskEnv& env, int i, int k, Ctx& c) {
     }
     View<double> Bp = Bv.shifted(0, c0);
     PH(16, stage_in(c.s.pnl, ldb, Bp, ry, w));
-    PH(17, ts_panel_qr(c.s.rp, c.s.pnl, ldb, ry, w, c.s.tau, c, std::is_same<S, float>::value));
+    PH(17, ts_panel_qr(c.s.rp, c.s.pnl, ldb, ry, w, c.s.tau, c));
     PH_BEGIN();
     gram_dense(c.s.pnl, ldb, ry, w, c.s.z, c);
     t_recur(c.s.z, c.s.tau, w, c.s.t, c);
@@ -645,17 +702,34 @@ __device__ void task_tsqrt(TaskEnv& env, int i, int k, Ctx& c) {
     }
   }
   if constexpr (std::is_same<S, float>::value) {
-    if (r != 0 && P.prep && env.tc) {
+    if (r != 0 && P.prep && env.tc && k + 1 < P.q) {
       // release the next update QR of this column now (it needs only R_kk),
       // then prepare the tensor-core operands for the updates TPMQRT(i,.,k)
+      // in a slot of the pool
+      __shared__ int slot_sh;
       __threadfence();
       __syncthreads();
-      if (i + 1 < P.p && threadIdx.x == 0 && P.task_base + dag_id_tsqrt(*env.dag, i, k) != P.withhold) {
-        const int sid = dag_id_tsqrt(*env.dag, i + 1, k);
-        release_task(P, *env.dag, sid);
-        env.skip_succ = sid;
+      if (threadIdx.x == 0) {
+        if (i + 1 < P.p && P.task_base + dag_id_tsqrt(*env.dag, i, k) != P.withhold) {
+          const int sid = dag_id_tsqrt(*env.dag, i + 1, k);
+          release_task(P, *env.dag, sid);
+          env.skip_succ = sid;
+        }
+        slot_sh = prep_acquire(P);
       }
-      PH(7, tsqrt_prep(env, i, k, c));
+      __syncthreads();
+      const int slot = slot_sh;
+      if (slot >= 0) {
+        PH(7, tsqrt_prep(env, i, k, prep_at(P, slot), c));
+        if (threadIdx.x == 0) {
+          // the q-k-1 updates TPMQRT(i,.,k) each release the slot once; they
+          // run after this task ends, so they see the slot it records
+          atomicExch(P.prep_ref + slot, P.q - k - 1);
+          atomicExch(P.prep_slot_of + prep_block(P, i, k), slot);
+          __threadfence();
+        }
+        __syncthreads();
+      }
     }
   }
 }
@@ -966,6 +1040,73 @@ __device__ void tc_apply_ts_group(TaskEnv& env, const double* Yg, long long ldy,
   c.fma += (double)wg * nc * b + (double)wg * nc * wg / 2 + (double)b * nc * wg;
 }
 
+// C (h x nc, FP64, ld ldc) <- Q_g^T C for a group of wg <= 128 consecutive
+// reflectors of a diagonal-tile QR (Section 3.4.1) whose vectors are given
+// explicitly, unit diagonal and zeros above it included (Yg, h x wg FP64,
+// ld ldy), with their inner 32-reflector T blocks at Tblk:
+//   Z = Y_g^T C;  W = T_g^T Z;  C -= Y_g W
+// on the tensor cores (3xTF32), T_g assembled from the inner blocks and the
+// Gram matrix G = Y_g^T Y_g.  Tg (128 x 128) and Zs (128 x nc) are global
+// scratch.
+__device__ void tc_apply_explicit_group(TaskEnv& env, const double* Yg, long long ldy, int h, int wg,
+                                        const double* Tblk, double* C, long long ldc, int nc, float* Tg, float* Zs,
+                                        Ctx& c) {
+  TcCtx& tc = *env.tc;
+  float* Gsm = tc.buf;                                   // staging area, idle between products
+  float* Tsm = tc.buf + 128 * 128;
+  float* Xsm = tc.buf + 2 * 128 * 128;
+  // G = Y_g^T Y_g
+  tc_gemm_tile(tc, 0, Yg, ldy, 1, wg, Yg, ldy, 1, wg, (wg + 15) & ~15, h);
+  tc_epilogue(tc, 0, (wg + 15) & ~15, [&](int r, int col, float v) {
+    if (r < 128 && col < 128) Gsm[r + col * 128] = v;
+  });
+  c.fma += (double)wg * wg * h / 2;
+  tc_group_t(Tblk, wg, Gsm, Tsm, Xsm, c);
+  for (int e = threadIdx.x; e < 128 * 128; e += BLR_NT) Tg[e] = Tsm[e];
+  __syncthreads();
+  for (int n0 = 0; n0 < nc; n0 += 256) {
+    const int nn = min(256, nc - n0), nn16 = (nn + 15) & ~15;
+    // Z = Y_g^T C
+    tc_gemm_tile(tc, 0, Yg, ldy, 1, wg, C + (size_t)n0 * ldc, ldc, 1, nn, nn16, h);
+    tc_epilogue(tc, 0, nn16, [&](int r, int col, float v) {
+      if (r < wg && col < nn) Zs[r + (size_t)(n0 + col) * 128] = v;
+    });
+    // W = T_g^T Z
+    tc_gemm_tile(tc, 0, (const float*)Tg, 128, 1, wg, (const float*)Zs + (size_t)n0 * 128, 128, 1, nn, nn16, wg);
+    tc_epilogue(tc, 0, nn16, [&](int r, int col, float v) {
+      if (r < wg && col < nn) Zs[r + (size_t)(n0 + col) * 128] = v;
+    });
+    // C -= Y_g W
+    for (int r0 = 0; r0 < h; r0 += TC_M) {
+      const int mrow = min(TC_M, h - r0);
+      tc_gemm_tile(tc, 0, Yg + r0, 1, ldy, mrow, (const float*)Zs + (size_t)n0 * 128, 128, 1, nn, nn16, wg);
+      tc_epilogue(tc, 0, nn16, [&](int r, int col, float v) {
+        if (r < mrow && col < nn) {
+          double* p = C + (r0 + r) + (size_t)(n0 + col) * ldc;
+          *p = ldg(p) - cvt<double>(v);
+        }
+      });
+    }
+  }
+  c.fma += (double)wg * nc * h + (double)wg * nc * wg / 2 + (double)h * nc * wg;
+}
+
+// The explicit vectors of the reflectors g0 .. g0 + wg - 1 of a diagonal
+// tile's QR (stored below the diagonal of tile A, b x b, ld b): rows g0 .. b
+// of those columns with the unit diagonal and zeros above it, into Yx
+// (b - g0 rows, ld b - g0).
+__device__ void explicit_reflectors(const double* A, int b, int g0, int wg, double* Yx) {
+  const int h = b - g0;
+  for (int e = threadIdx.x; e < h * wg; e += BLR_NT) {
+    const int r = e % h, l = e / h;
+    double v = 0.0;
+    if (r > l) v = ldg(A + (g0 + r) + (size_t)(g0 + l) * b);
+    else if (r == l) v = 1.0;
+    Yx[e] = v;
+  }
+  __syncthreads();
+}
+
 // [Ct (b x nc, ld ldt); Cb (b x nc, ld ldb)] <- Q^T [Ct; Cb] for the dense
 // reflector block of a TSQRT, Q = I - [I; Y] T [I; Y]^T with Y b x b dense
 // (Section 3.4.4, Eq. 21), in groups of 128 reflectors.  Products on the
@@ -1039,13 +1180,15 @@ __device__ void task_tpmqrt(TaskEnv& env, int i, int j, int k, Ctx& c) {
     return;
   }
   if (rY == 0) return;
+  // the operands the TSQRT prepared for this reflector block, if it found a slot
+  const int slot = P.prep ? __ldcg(P.prep_slot_of + prep_block(P, i, k)) : -1;
+  const float* prep = slot >= 0 ? prep_at(P, slot) : nullptr;
   if (rY < 0 && (rR < 0 || rA < 0) && env.tc) {
-    PH(6, tpmqrt_tc_dense(env, Yt, Tik, P.prep ? prep_ptr(P, i, k) : nullptr, Rt, rR, At, rA,
-                          rank_ptr(P, k, j), rank_ptr(P, i, j), c));
+    PH(6, tpmqrt_tc_dense(env, Yt, Tik, prep, Rt, rR, At, rA, rank_ptr(P, k, j), rank_ptr(P, i, j), c));
     return;
   }
   // a low-rank reflector block whose TSQRT prepared tensor-core operands
-  env.prep_slot = (P.prep && env.tc && rY > 0) ? prep_ptr(P, i, k) : nullptr;
+  env.prep_slot = (env.tc && rY > 0) ? prep : nullptr;
   // mixed: FP32 copies of the operands, FP32 arithmetic, results back to FP64
   float* Yf = (float*)env.alloc((size_t)b * b / 2);
   float* Tf = (float*)env.alloc((size_t)BLR_NB * b / 2);
@@ -1221,6 +1364,12 @@ __global__ void __launch_bounds__(BLR_NT, 1) k_factor(SchedParams P) {
     if (threadIdx.x == 0) atomicMax(P.slab_peak, (unsigned long long)env.peak);
     __threadfence();
     __syncthreads();
+    // an update has finished with its reflector block's prepared operands
+    // (every read of them completed inside the body): return the slot once
+    if (kTensor && type == TASK_TPMQRT && threadIdx.x == 0 && Pm->prep) {
+      const int slot = __ldcg(Pm->prep_slot_of + prep_block(*Pm, i, k));
+      if (slot >= 0) atomicSub(Pm->prep_ref + slot, 1);
+    }
     if (threadIdx.x == 0 && type >= 0) {
       const unsigned long long t_end = gtimer();
       if (P.trace) {

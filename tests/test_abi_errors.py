@@ -149,7 +149,8 @@ def test_qr_entry_points_reject_on_host(L):
     nortol = _opts(b=128, tol=0.0, rec_tol=0.0)
     assert L.blr_batch_plan_create(arr, 2, ctypes.byref(nortol), ctypes.byref(plan), None) == INVALID
     assert "rec_tol" in blr.blr_last_error()
-    for kw, msg in [({"trace": -1}, "trace"), ({"test_withhold": -3}, "test_withhold")]:
+    for kw, msg in [({"trace": -1}, "trace"), ({"test_withhold": -3}, "test_withhold"),
+                    ({"prep_slots": -1}, "prep_slots")]:
         neg = _opts(b=128, **kw)
         assert L.blr_batch_plan_create(arr, 2, ctypes.byref(neg), ctypes.byref(plan), None) == INVALID
         assert msg in blr.blr_last_error()
