@@ -29,6 +29,19 @@
 #define PH_END(id)                                                               \
   __syncthreads();                                                               \
   if (threadIdx.x == 0) atomicAdd(env.P->phase + (id), tc_gtimer() - ph_b0_);
+// a second, independently named pair for regions that share a scope
+#define PH_BEGIN2()                      \
+  __syncthreads();                       \
+  const unsigned long long ph_b2_ = tc_gtimer();
+#define PH_END2(id)                                                              \
+  __syncthreads();                                                               \
+  if (threadIdx.x == 0) atomicAdd(env.P->phase + (id), tc_gtimer() - ph_b2_);
+#define PH_BEGIN3()                      \
+  __syncthreads();                       \
+  const unsigned long long ph_b3_ = tc_gtimer();
+#define PH_END3(id)                                                              \
+  __syncthreads();                                                               \
+  if (threadIdx.x == 0) atomicAdd(env.P->phase + (id), tc_gtimer() - ph_b3_);
 #else
 #define PH(id, ...) \
   do {              \
@@ -36,6 +49,10 @@
   } while (0)
 #define PH_BEGIN()
 #define PH_END(id)
+#define PH_BEGIN2()
+#define PH_END2(id)
+#define PH_BEGIN3()
+#define PH_END3(id)
 #endif
 
 namespace {
@@ -389,7 +406,7 @@ __device__ void tsqrt_prep(TaskEnv& env, int i, int k, float* slot, Ctx& c) {
   fence_async_global();
   __syncthreads();
   PH_END(24);
-  PH_BEGIN();
+  PH_BEGIN2();
   // G = Y^T Y (FP32, ld b, upper block triangle)
   float* G = (float*)env.alloc((size_t)b * b / 2);
   float* T = (float*)env.alloc((size_t)b * b / 2);
@@ -406,14 +423,14 @@ __device__ void tsqrt_prep(TaskEnv& env, int i, int k, float* slot, Ctx& c) {
     }
   }
   c.fma += (double)b * b * Kt / 2;
-  PH_END(25);
+  PH_END2(25);
   // T from its 32 x 32 diagonal blocks by merging neighbouring blocks of
   // h reflectors into blocks of 2h: for the product of the compact WY forms
   // (I - Y1 T1 Y1^T)(I - Y2 T2 Y2^T) = I - [Y1 Y2] T [Y1 Y2]^T the new
   // off-diagonal block is T12 = -T1 (Y1^T Y2) T2 = -T1 G12 T2 (Eq. 3 for a
   // block of reflectors, the Schreiber-Van Loan recurrence taken a block at
   // a time); each merge is two FP32 products in shared-memory tiles.
-  PH_BEGIN();
+  PH_BEGIN3();
   for (int e = threadIdx.x; e < b * b; e += BLR_NT) {
     const int a = e % b, l = e / b;
     T[e] = ((a >> 5) == (l >> 5) && a <= l) ? cvt<float>(ldg(Tk + (size_t)l * BLR_NB + (a & 31))) : 0.f;
@@ -434,7 +451,7 @@ __device__ void tsqrt_prep(TaskEnv& env, int i, int k, float* slot, Ctx& c) {
       __syncthreads();
     }
   }
-  PH_END(26);
+  PH_END3(26);
   PH(27, tc_canon(tt_h, tt_l, Rp, b, (const float*)T, b, 1, b, b));   // (a, k) = T(k, a) = T[k + a b]
   fence_async_global();
   __threadfence();

@@ -296,9 +296,12 @@ def test_prepared_operand_pool_smaller_than_the_blocks(lib):
         opts.prep_slots = slots
         fac = lib.blr_qr(lib.blr_matrix_import(m, n, b, ranks, tiles), opts)
         st = lib.blr_stats(fac)
-        if slots:
-            assert st["prep_slots"] == slots and st["prep_misses"] > 0, st
-        else:
-            assert st["prep_slots"] == n_blocks and st["prep_misses"] == 0, st
+        assert st["prep_slots"] == (slots or n_blocks), st
+        if slots == 0:
+            assert st["prep_misses"] == 0, st
+        if slots == 1:
+            # the next update QR of a column starts while the previous one
+            # still prepares into the only slot
+            assert st["prep_misses"] > 0, st
         _elementwise(lib, fac, fo, ref.dense(), p, q, b, eps, True, kappa)
         fac.destroy()
