@@ -486,16 +486,20 @@ __device__ void tc_apply_prepared(TaskEnv& env, const float* slot, double* Ct, d
                    cc_l + (size_t)n0 * TC_KC, cs, nn16, nchunk));
       {
       PH_BEGIN();
-      tc_epilogue16(tc, 0, nn16, [&](int r, int col, const float* v) {
-        const int a = m0 + r;
-        if (a >= b) return;
-        double ct[16];
+      tc_epilogue16_pf<double>(
+          tc, 0, nn16,
+          [&](int r, int col, double* ct) {
+            const int a = m0 + r;
 #pragma unroll
-        for (int u = 0; u < 16; u++) ct[u] = (col + u < nn) ? ldg(Ct + a + (size_t)(n0 + col + u) * b) : 0.0;
+            for (int u = 0; u < 16; u++) ct[u] = (a < b && col + u < nn) ? ldg(Ct + a + (size_t)(n0 + col + u) * b) : 0.0;
+          },
+          [&](int r, int col, const float* v, const double* ct) {
+            const int a = m0 + r;
+            float z[16];
 #pragma unroll
-        for (int u = 0; u < 16; u++)
-          if (col + u < nn) tc_canon_put(zc_h, zc_l, Rp, n0 + col + u, a, v[u] + cvt<float>(ct[u]));
-      });
+            for (int u = 0; u < 16; u++) z[u] = v[u] + cvt<float>(ct[u]);
+            tc_canon_put16(zc_h, zc_l, Rp, n0 + col, a, z, nn - col, a < b);
+          });
       PH_END(14);
       }
     }
@@ -511,20 +515,22 @@ __device__ void tc_apply_prepared(TaskEnv& env, const float* slot, double* Ct, d
                    zc_l + (size_t)n0 * TC_KC, cs, nn16, kch));
       {
       PH_BEGIN();
-      tc_epilogue16(tc, 0, nn16, [&](int r, int col, const float* v) {
-        const int a = m0 + r;
-        if (a >= b) return;
-        double ct[16];
+      tc_epilogue16_pf<double>(
+          tc, 0, nn16,
+          [&](int r, int col, double* ct) {
+            const int a = m0 + r;
 #pragma unroll
-        for (int u = 0; u < 16; u++) ct[u] = (col + u < nn) ? ldg(Ct + a + (size_t)(n0 + col + u) * b) : 0.0;
+            for (int u = 0; u < 16; u++) ct[u] = (a < b && col + u < nn) ? ldg(Ct + a + (size_t)(n0 + col + u) * b) : 0.0;
+          },
+          [&](int r, int col, const float* v, const double* ct) {
+            const int a = m0 + r;
+            if (a < b) {
 #pragma unroll
-        for (int u = 0; u < 16; u++) {
-          if (col + u < nn) {
-            Ct[a + (size_t)(n0 + col + u) * b] = ct[u] - cvt<double>(v[u]);
-            tc_canon_put(cc_h, cc_l, Rp, n0 + col + u, a, v[u]);    // W as an operand (rows = n, K = a)
-          }
-        }
-      });
+              for (int u = 0; u < 16; u++)
+                if (col + u < nn) Ct[a + (size_t)(n0 + col + u) * b] = ct[u] - cvt<double>(v[u]);
+            }
+            tc_canon_put16(cc_h, cc_l, Rp, n0 + col, a, v, nn - col, a < b);   // W as an operand (rows = n, K = a)
+          });
       PH_END(14);
       }
     }
@@ -539,16 +545,21 @@ __device__ void tc_apply_prepared(TaskEnv& env, const float* slot, double* Ct, d
                    cc_l + (size_t)n0 * TC_KC, cs, nn16, nchunk));
       {
       PH_BEGIN();
-      tc_epilogue16(tc, 0, nn16, [&](int r, int col, const float* v) {
-        const int rr = m0 + r;
-        if (rr >= b) return;
-        double cb[16];
+      tc_epilogue16_pf<double>(
+          tc, 0, nn16,
+          [&](int r, int col, double* cb) {
+            const int rr = m0 + r;
 #pragma unroll
-        for (int u = 0; u < 16; u++) cb[u] = (col + u < nn) ? ldg(Cb + rr + (size_t)(n0 + col + u) * b) : 0.0;
+            for (int u = 0; u < 16; u++)
+              cb[u] = (rr < b && col + u < nn) ? ldg(Cb + rr + (size_t)(n0 + col + u) * b) : 0.0;
+          },
+          [&](int r, int col, const float* v, const double* cb) {
+            const int rr = m0 + r;
+            if (rr >= b) return;
 #pragma unroll
-        for (int u = 0; u < 16; u++)
-          if (col + u < nn) Cb[rr + (size_t)(n0 + col + u) * b] = cb[u] - cvt<double>(v[u]);
-      });
+            for (int u = 0; u < 16; u++)
+              if (col + u < nn) Cb[rr + (size_t)(n0 + col + u) * b] = cb[u] - cvt<double>(v[u]);
+          });
       PH_END(14);
       }
     }

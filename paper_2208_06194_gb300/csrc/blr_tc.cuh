@@ -145,6 +145,18 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
   for (int i = 0; i < 16; i++) v[i] = __uint_as_float(r[i]);
 }
 
+// The same load issued without waiting; tmem_wait_ld() waits for all of a
+// thread's outstanding TMEM loads (several loads then share one wait).
+__device__ __forceinline__ void tmem_ld16_nowait(uint32_t taddr, uint32_t* r) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr)
+      : "memory");
+}
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
 // ---- operand staging ----------------------------------------------------------
 __device__ __forceinline__ float tf32_hi(float x) {
   uint32_t u;
@@ -494,6 +506,77 @@ __device__ void tc_epilogue16(const TcCtx& t, uint32_t col0, int ncol, F f) {
   }
   tc_fence_before();
   __syncthreads();
+}
+
+// As tc_epilogue16, with a caller's global loads for the same 16 columns
+// issued before the accumulator is read, so that the global and the TMEM
+// latencies overlap: pre(row, col, g) fills g[0..15] (type G), then
+// post(row, col, v, g) receives the accumulator values v[0..15].  Both are
+// called by every thread (rows past the product included: they must take
+// part in warp-wide exchanges).
+template <class G, class Pre, class Post>
+__device__ void tc_epilogue16_pf(const TcCtx& t, uint32_t col0, int ncol, Pre pre, Post post) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int quarter = warp & 3, half = warp >> 2;
+  const int row = quarter * 32 + lane;
+  const int nblk = ncol / 16;
+  for (int cb = half; cb < nblk; cb += 2) {
+    G g[16];
+    pre(row, cb * 16, g);
+    uint32_t rv[16], rx[16];
+    const uint32_t a = t.tmem + ((uint32_t)(quarter * 32) << 16) + col0 + cb * 16;
+    tmem_ld16_nowait(a, rv);
+    tmem_ld16_nowait(a + TC_XCOL, rx);
+    tmem_wait_ld();
+    float v[16];
+#pragma unroll
+    for (int i = 0; i < 16; i++) v[i] = __uint_as_float(rv[i]) + __uint_as_float(rx[i]);
+    post(row, cb * 16, v, g);
+  }
+  tc_fence_before();
+  __syncthreads();
+}
+
+// Elements (n, a) = v[u] for n = nbase + u (u < 16) of a canonical (hi, lo)
+// operand of R rows, one tile row a per lane, lanes of a warp on
+// consecutive a with a % 4 == lane % 4.  The four lanes of a's group of four
+// exchange their values (four shuffle rounds per four columns) so that each
+// stores the 16-byte run (n, a0 .. a0 + 3) of one column: full 32-byte
+// sectors instead of 4-byte pieces.  Columns u >= nvalid and groups whose
+// rows are past the operand (avalid false) are not stored; every lane of the
+// warp must call this.
+__device__ __forceinline__ void tc_canon_put16(float* hi, float* lo, int R, int nbase, int a, const float* v,
+                                               int nvalid, bool avalid) {
+  const int lane = threadIdx.x & 31, j = lane & 3, a0 = a & ~3;
+#pragma unroll
+  for (int qb = 0; qb < 4; qb++) {
+    float w[4];
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+      // round k: this lane sends its value of column 4 qb + ((j - k) & 3) and
+      // receives from lane (j + k) & 3 of its group that lane's value of
+      // column 4 qb + j, i.e. row a0 + ((j + k) & 3) of this lane's column
+      const int si = (j - k) & 3;
+      const float sv = si == 0 ? v[4 * qb] : si == 1 ? v[4 * qb + 1] : si == 2 ? v[4 * qb + 2] : v[4 * qb + 3];
+      w[k] = __shfl_sync(FULLMASK, sv, (lane & ~3) | ((j + k) & 3));
+    }
+    // rows a0 + i: w[(i - j) & 3]
+    float rowv[4];
+#pragma unroll
+    for (int i = 0; i < 4; i++) {
+      const int kk = (i - j) & 3;
+      rowv[i] = kk == 0 ? w[0] : kk == 1 ? w[1] : kk == 2 ? w[2] : w[3];
+    }
+    const int u = 4 * qb + j;
+    if (avalid && u < nvalid) {
+      float h[4], l[4];
+#pragma unroll
+      for (int i = 0; i < 4; i++) tc_split(rowv[i], h[i], l[i]);
+      const size_t off = canon_index(R, nbase + u, a0);
+      *reinterpret_cast<float4*>(hi + off) = make_float4(h[0], h[1], h[2], h[3]);
+      *reinterpret_cast<float4*>(lo + off) = make_float4(l[0], l[1], l[2], l[3]);
+    }
+  }
 }
 
 // Reads the TC_M x ncol accumulator at TMEM columns [col0, col0 + ncol)
