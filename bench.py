@@ -113,6 +113,9 @@ def roofline(st, k_sec, prec_is_fp64):
 SIZES = {
     "full": dict(m=65536, n=32768, b=512, seed_x=301, seed_y=302),
     "small": dict(m=8192, n=4096, b=512, seed_x=301, seed_y=302),
+    # the 131072 x 65536 kernel matrix of the differentiable least-squares
+    # workload (points seeds 501/502, right-hand sides seed 503), at b = 512
+    "target": dict(m=131072, n=65536, b=512, seed_x=501, seed_y=502),
 }
 
 
@@ -137,6 +140,10 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-compare-fp64", action="store_true",
                     help="skip the FP64 factorization timed beside the mixed one (N = 1)")
+    ap.add_argument("--lstsq-rhs", type=int, default=0,
+                    help="with the FP64 factor (the FP64 leg, or the main one with --precision fp64): also "
+                         "solve min ||A~ X - B|| for this many N(0,1) right-hand sides (seed 503) with one "
+                         "refinement step, timed")
     ap.add_argument("--fp64-steps", type=int, default=3, help="timed FP64 factorizations (median)")
     ap.add_argument("--fp64-warmup", type=int, default=1)
     ap.add_argument("--scratch-b2", type=int, default=0, help="per-CTA scratch in units of b*b doubles")
@@ -242,6 +249,29 @@ def probes(blr, fac, a_clone, pr, torch, dev, k=16, seed=5):
     blr.blr_apply_qt(fac, qz, trans=0)
     orth = float(torch.linalg.norm(qz[:n] - zf) / np.sqrt(k) / np.sqrt(n)) if k else None
     return res_a, res_at, orth
+
+
+def lstsq_check(blr, fac, a_t, pr, k, torch, seed=503):
+    """X = argmin ||A~ X - B||_F for k N(0,1) right-hand sides with one step
+    of refinement (blr_lstsq), timed with CUDA events; the residual and the
+    optimality of X (Q_1^T r = 0, i.e. A~^T r = R^T Q_1^T r = 0)."""
+    g = torch.Generator(device="cpu").manual_seed(seed)
+    bmat = blr.to_fortran(torch.randn((pr.m, k), generator=g, dtype=torch.float64))
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    x = blr.blr_lstsq(fac, bmat, a_orig=a_t, refine_steps=1)
+    e1.record()
+    e1.synchronize()
+    r = bmat - blr.blr_matmul(a_t, x)
+    qtr = blr.fortran_empty(pr.m, k)
+    qtr.copy_(r)
+    blr.blr_apply_qt(fac, qtr, trans=0)
+    rn = float(torch.linalg.norm(r))
+    return {"rhs": k, "seconds": e0.elapsed_time(e1) * 1e-3, "refine_steps": 1,
+            "residual_rel": rn / float(torch.linalg.norm(bmat)),
+            "optimality": float(torch.linalg.norm(qtr[:pr.n])) / rn}
 
 
 _SAMPLE = {}
@@ -570,7 +600,15 @@ def main():
     st = blr.blr_stats(fac)
     t_step = max_over_ranks(statistics.median(times), world, dist, dev)
     res_a, res_at, orth = probes(blr, fac, a0, pr, torch, dev)
+    ls_main = None
+    if args.lstsq_rhs > 0 and prec == blr.BLR_PREC_FP64:
+        ls_main = lstsq_check(blr, fac, a0, pr, args.lstsq_rhs, torch)
     fac.destroy()
+    if args.size == "target":
+        # 68.7 GB of tiles per copy: free the mixed path's input before the
+        # FP64 leg compresses its own (the end-to-end leg is skipped here)
+        a0.destroy()
+        args.no_e2e = True
 
     # FP64 comparison at the same tolerance (mixed runs only)
     fp64 = None
@@ -590,13 +628,14 @@ def main():
         t64 = statistics.median(t64s)
         r64 = probes(blr, f64, a64, pr, torch, dev)
         st64 = blr.blr_stats(f64)
+        ls = lstsq_check(blr, f64, a64, pr, args.lstsq_rhs, torch) if args.lstsq_rhs > 0 else None
         a64.destroy()
         fp64 = {"seconds": t64, "seconds_all": t64s, "warmup": args.fp64_warmup,
                 "res_A": r64[0], "res_At": r64[1], "orth": r64[2],
                 "gflops_counted": st64["flops"][4] / 1e9,
                 "roofline": roofline(st64, statistics.median(t64s), True),
                 "meets_10tol": bool(r64[0] <= 10 * args.tol), "mixed_speedup": t64 / t_step,
-                "dense_rank": args.dense_rank_fp64}
+                "dense_rank": args.dense_rank_fp64, "lstsq": ls}
         f64.destroy()
 
     # end to end through host buffers: import (H2D) + blr_qr + export (D2H)
@@ -643,7 +682,7 @@ def main():
         "data": "synthetic",
         "config": {"workload": workload_name(args), "global_batch": world, "precision": args.precision,
                    "dense_rank": args.dense_rank, "parallelism": "replicas" if world > 1 else "single",
-                   "l2": "inputs larger than L2 (17 GB of tiles per step)"},
+                   "l2": f"inputs larger than L2 ({s['m'] * s['n'] * 8 / 1e9:.0f} GB of tiles per step)"},
         "res_A": res_a, "res_At": res_at, "orth": orth,
         "ranks": {"before": {"n_dense": st_a["n_dense"], "mean": st_a["mean_rank"], "max": st_a["max_rank"]},
                   "after": {"n_dense": st["n_dense"], "mean": st["mean_rank"], "max": st["max_rank"]}},
@@ -657,6 +696,7 @@ def main():
         "e2e": e2e,
         "cpu_baseline": cpu,
         "fp64": fp64,
+        "lstsq": ls_main,
     }
     print(json.dumps(line), flush=True)
     if world > 1:

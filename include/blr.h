@@ -445,6 +445,22 @@ int blr_dag_task(int p, int q, int id, int* task, int* succ, int cap);
 int blr_tc_gemm_selftest(const double* a_dev, int lda, const double* b_dev, int ldb, double* d_dev,
                          int ldd, int m, int n, int k, void* stream);
 
+/*
+ * blr_tc_update_bench -- diagnostic timing of the dense prepared trapezoidal
+ * update on its own (Section 3.4.4 with a dense reflector block and dense
+ * tiles; the mixed path's tensor-core body, 2.5 b^3 multiply-adds): ctas
+ * CTAs each repeat the update reps times on their own b x b tiles with one
+ * shared slot of prepared operands, filled with synthetic bounded values.
+ * variant selects an implementation variant of its conversion and
+ * epilogues (0, 1, 2, 3, 4, 6, 9, 11 or 15; 0 is the factorization's).
+ * *ms_per_update (host) receives the mean device time of one update per
+ * CTA; *aggregate_tflops (host, may be NULL) the algorithmic rate of the
+ * whole launch.  Errors: BLR_ERR_INVALID (b not a multiple of 128 in
+ * [128, 512], ctas or reps < 1, unknown variant), BLR_ERR_OOM, BLR_ERR_CUDA,
+ * BLR_ERR_TIMEOUT.
+ */
+int blr_tc_update_bench(int b, int ctas, int reps, int variant, double* ms_per_update, double* aggregate_tflops);
+
 #ifdef __cplusplus
 }
 #endif

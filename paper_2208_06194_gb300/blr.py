@@ -96,6 +96,7 @@ _SIGS = {
     "blr_batch_selfcheck": (_I, [_IP, _IP, _I, ctypes.c_uint]),
     "blr_dag_task": (_I, [_I, _I, _I, _IP, _IP, _I]),
     "blr_tc_gemm_selftest": (_I, [_P, _I, _P, _I, _P, _I, _I, _I, _I, _P]),
+    "blr_tc_update_bench": (_I, [_I, _I, _I, _I, _DP, _DP]),
 }
 EXPORTED = tuple(_SIGS)
 
@@ -481,3 +482,15 @@ def blr_tc_gemm_selftest(a, bm, stream=None):
     _check(lib().blr_tc_gemm_selftest(a.data_ptr(), a.stride(1), bm.data_ptr(), bm.stride(1), d.data_ptr(),
                                       d.stride(1), m, n, k, _stream(stream)))
     return d
+
+
+def blr_tc_update_bench(b: int = 512, ctas: int | None = None, reps: int = 8, variant: int = 0) -> dict:
+    """Diagnostic timing of the dense prepared update (ms per update per CTA,
+    aggregate algorithmic TFLOP/s); ctas defaults to the SM count."""
+    if ctas is None:
+        import torch
+        ctas = torch.cuda.get_device_properties(0).multi_processor_count
+    ms, tf = ctypes.c_double(0.0), ctypes.c_double(0.0)
+    _check(lib().blr_tc_update_bench(b, ctas, reps, variant, ctypes.byref(ms), ctypes.byref(tf)))
+    return {"b": b, "ctas": ctas, "reps": reps, "variant": variant, "ms_per_update": ms.value,
+            "aggregate_tflops": tf.value}

@@ -55,6 +55,12 @@
 #define PH_END3(id)
 #endif
 
+// The variant of the dense prepared update the factorization runs (see
+// tc_apply_prepared; chosen by measurement with blr_tc_update_bench).
+#ifndef BLR_TC_UPDATE_VARIANT
+#define BLR_TC_UPDATE_VARIANT 0
+#endif
+
 namespace {
 
 // Bump allocator over the CTA's private scratch slab.  The slab holds
@@ -429,7 +435,7 @@ __device__ void tsqrt_prep(TaskEnv& env, int i, int k, float* slot, Ctx& c) {
   // (I - Y1 T1 Y1^T)(I - Y2 T2 Y2^T) = I - [Y1 Y2] T [Y1 Y2]^T the new
   // off-diagonal block is T12 = -T1 (Y1^T Y2) T2 = -T1 G12 T2 (Eq. 3 for a
   // block of reflectors, the Schreiber-Van Loan recurrence taken a block at
-  // a time); each merge is two FP32 products in shared-memory tiles.
+  // a time); each merge is two products on the tensor cores.
   PH_BEGIN3();
   for (int e = threadIdx.x; e < b * b; e += BLR_NT) {
     const int a = e % b, l = e / b;
@@ -440,15 +446,26 @@ __device__ void tsqrt_prep(TaskEnv& env, int i, int k, float* slot, Ctx& c) {
   const int ldx = b / 2;
   for (int h = BLR_NB; h < b; h *= 2) {
     for (int j0 = 0; j0 + h < b; j0 += 2 * h) {
-      const int h2 = min(h, b - j0 - h);
+      const int h2 = min(h, b - j0 - h), h216 = (h2 + 15) & ~15;
       // X = G(j0:j0+h, j0+h:j0+h+h2) T(j0+h:j0+h+h2, j0+h:j0+h+h2)
-      gemm(h, h2, h2, 1.f, G + j0 + (size_t)(j0 + h) * b, b, false, (const float*)T + (j0 + h) + (size_t)(j0 + h) * b,
-           b, false, 0.f, X, ldx, c);
-      __syncthreads();
+      for (int m0 = 0; m0 < h; m0 += TC_M) {
+        const int mrow = min(TC_M, h - m0);
+        tc_gemm_tile(tc, 0, (const float*)G + j0 + m0 + (size_t)(j0 + h) * b, 1, b, mrow,
+                     (const float*)T + (j0 + h) + (size_t)(j0 + h) * b, b, 1, h2, h216, h2);
+        tc_epilogue(tc, 0, h216, [&](int r, int col, float v) {
+          if (r < mrow && col < h2) X[(m0 + r) + (size_t)col * ldx] = v;
+        });
+      }
       // T(j0:j0+h, j0+h:j0+h+h2) = -T(j0:j0+h, j0:j0+h) X
-      gemm(h, h2, h, -1.f, (const float*)T + j0 + (size_t)j0 * b, b, false, (const float*)X, ldx, false, 0.f,
-           T + j0 + (size_t)(j0 + h) * b, b, c);
-      __syncthreads();
+      for (int m0 = 0; m0 < h; m0 += TC_M) {
+        const int mrow = min(TC_M, h - m0);
+        tc_gemm_tile(tc, 0, (const float*)T + j0 + m0 + (size_t)j0 * b, 1, b, mrow, (const float*)X, ldx, 1, h2,
+                     h216, h);
+        tc_epilogue(tc, 0, h216, [&](int r, int col, float v) {
+          if (r < mrow && col < h2) T[(j0 + m0 + r) + (size_t)(j0 + h + col) * b] = -v;
+        });
+      }
+      c.fma += (double)h * h2 * h2 + (double)h * h2 * h;
     }
   }
   PH_END3(26);
@@ -462,6 +479,13 @@ __device__ void tsqrt_prep(TaskEnv& env, int i, int k, float* slot, Ctx& c) {
 // block with prepared operands: Z = Ct + Y^T Cb, W = T^T Z, Ct -= W,
 // Cb -= Y W, all b reflectors at once (three b x b x b products, the second
 // one triangular), on the tensor cores with bulk-copied operands.
+// V selects implementation variants of the conversion and the epilogues
+// (measured against each other by blr_tc_update_bench): bit 0, Cb is
+// converted by K-major tiles with coalesced loads; bit 3 with it, those
+// tiles are stored through the four-lane exchange; bit 1, the epilogues
+// issue their FP64 loads before reading TMEM; bit 2, the Z and W operands
+// are stored through the four-lane exchange.
+template <int V = 0>
 __device__ void tc_apply_prepared(TaskEnv& env, const float* slot, double* Ct, double* Cb, Ctx& c) {
   const SchedParams& P = *env.P;
   TcCtx& tc = *env.tc;
@@ -474,7 +498,11 @@ __device__ void tc_apply_prepared(TaskEnv& env, const float* slot, double* Ct, d
   float* cc_l = (float*)env.alloc(op / 2);
   float* zc_h = (float*)env.alloc(op / 2);    // Z as an operand (rows = columns n, K = reflectors)
   float* zc_l = (float*)env.alloc(op / 2);
-  PH(12, tc_canon(cc_h, cc_l, Rp, b, (const double*)Cb, b, 1, b, b));    // (n, r) = Cb[r + n b]
+  if constexpr ((V & 1) != 0) {
+    PH(12, tc_canon_kmajor(cc_h, cc_l, Rp, b, (const double*)Cb, b, b, b, (V & 8) != 0));
+  } else {
+    PH(12, tc_canon(cc_h, cc_l, Rp, b, (const double*)Cb, b, 1, b, b));    // (n, r) = Cb[r + n b]
+  }
   fence_async_global();
   __syncthreads();
   const int nchunk = b / TC_KC;
@@ -486,20 +514,40 @@ __device__ void tc_apply_prepared(TaskEnv& env, const float* slot, double* Ct, d
                    cc_l + (size_t)n0 * TC_KC, cs, nn16, nchunk));
       {
       PH_BEGIN();
-      tc_epilogue16_pf<double>(
-          tc, 0, nn16,
-          [&](int r, int col, double* ct) {
-            const int a = m0 + r;
+      if constexpr ((V & 6) == 0) {
+        tc_epilogue16(tc, 0, nn16, [&](int r, int col, const float* v) {
+          const int a = m0 + r;
+          if (a >= b) return;
+          double ct[16];
 #pragma unroll
-            for (int u = 0; u < 16; u++) ct[u] = (a < b && col + u < nn) ? ldg(Ct + a + (size_t)(n0 + col + u) * b) : 0.0;
-          },
-          [&](int r, int col, const float* v, const double* ct) {
-            const int a = m0 + r;
-            float z[16];
+          for (int u = 0; u < 16; u++) ct[u] = (col + u < nn) ? ldg(Ct + a + (size_t)(n0 + col + u) * b) : 0.0;
 #pragma unroll
-            for (int u = 0; u < 16; u++) z[u] = v[u] + cvt<float>(ct[u]);
-            tc_canon_put16(zc_h, zc_l, Rp, n0 + col, a, z, nn - col, a < b);
-          });
+          for (int u = 0; u < 16; u++)
+            if (col + u < nn) tc_canon_put(zc_h, zc_l, Rp, n0 + col + u, a, v[u] + cvt<float>(ct[u]));
+        });
+      } else {
+        tc_epilogue16_pf<double>(
+            tc, 0, nn16,
+            [&](int r, int col, double* ct) {
+              const int a = m0 + r;
+#pragma unroll
+              for (int u = 0; u < 16; u++)
+                ct[u] = (a < b && col + u < nn) ? ldg(Ct + a + (size_t)(n0 + col + u) * b) : 0.0;
+            },
+            [&](int r, int col, const float* v, const double* ct) {
+              const int a = m0 + r;
+              float z[16];
+#pragma unroll
+              for (int u = 0; u < 16; u++) z[u] = v[u] + cvt<float>(ct[u]);
+              if constexpr ((V & 4) != 0) {
+                tc_canon_put16(zc_h, zc_l, Rp, n0 + col, a, z, nn - col, a < b);
+              } else if (a < b) {
+#pragma unroll
+                for (int u = 0; u < 16; u++)
+                  if (col + u < nn) tc_canon_put(zc_h, zc_l, Rp, n0 + col + u, a, z[u]);
+              }
+            });
+      }
       PH_END(14);
       }
     }
@@ -515,22 +563,46 @@ __device__ void tc_apply_prepared(TaskEnv& env, const float* slot, double* Ct, d
                    zc_l + (size_t)n0 * TC_KC, cs, nn16, kch));
       {
       PH_BEGIN();
-      tc_epilogue16_pf<double>(
-          tc, 0, nn16,
-          [&](int r, int col, double* ct) {
-            const int a = m0 + r;
+      if constexpr ((V & 6) == 0) {
+        tc_epilogue16(tc, 0, nn16, [&](int r, int col, const float* v) {
+          const int a = m0 + r;
+          if (a >= b) return;
+          double ct[16];
 #pragma unroll
-            for (int u = 0; u < 16; u++) ct[u] = (a < b && col + u < nn) ? ldg(Ct + a + (size_t)(n0 + col + u) * b) : 0.0;
-          },
-          [&](int r, int col, const float* v, const double* ct) {
-            const int a = m0 + r;
-            if (a < b) {
+          for (int u = 0; u < 16; u++) ct[u] = (col + u < nn) ? ldg(Ct + a + (size_t)(n0 + col + u) * b) : 0.0;
+#pragma unroll
+          for (int u = 0; u < 16; u++) {
+            if (col + u < nn) {
+              Ct[a + (size_t)(n0 + col + u) * b] = ct[u] - cvt<double>(v[u]);
+              tc_canon_put(cc_h, cc_l, Rp, n0 + col + u, a, v[u]);    // W as an operand (rows = n, K = a)
+            }
+          }
+        });
+      } else {
+        tc_epilogue16_pf<double>(
+            tc, 0, nn16,
+            [&](int r, int col, double* ct) {
+              const int a = m0 + r;
 #pragma unroll
               for (int u = 0; u < 16; u++)
-                if (col + u < nn) Ct[a + (size_t)(n0 + col + u) * b] = ct[u] - cvt<double>(v[u]);
-            }
-            tc_canon_put16(cc_h, cc_l, Rp, n0 + col, a, v, nn - col, a < b);   // W as an operand (rows = n, K = a)
-          });
+                ct[u] = (a < b && col + u < nn) ? ldg(Ct + a + (size_t)(n0 + col + u) * b) : 0.0;
+            },
+            [&](int r, int col, const float* v, const double* ct) {
+              const int a = m0 + r;
+              if (a < b) {
+#pragma unroll
+                for (int u = 0; u < 16; u++)
+                  if (col + u < nn) Ct[a + (size_t)(n0 + col + u) * b] = ct[u] - cvt<double>(v[u]);
+              }
+              if constexpr ((V & 4) != 0) {
+                tc_canon_put16(cc_h, cc_l, Rp, n0 + col, a, v, nn - col, a < b);
+              } else if (a < b) {
+#pragma unroll
+                for (int u = 0; u < 16; u++)
+                  if (col + u < nn) tc_canon_put(cc_h, cc_l, Rp, n0 + col + u, a, v[u]);
+              }
+            });
+      }
       PH_END(14);
       }
     }
@@ -545,21 +617,34 @@ __device__ void tc_apply_prepared(TaskEnv& env, const float* slot, double* Ct, d
                    cc_l + (size_t)n0 * TC_KC, cs, nn16, nchunk));
       {
       PH_BEGIN();
-      tc_epilogue16_pf<double>(
-          tc, 0, nn16,
-          [&](int r, int col, double* cb) {
-            const int rr = m0 + r;
+      if constexpr ((V & 2) == 0) {
+        tc_epilogue16(tc, 0, nn16, [&](int r, int col, const float* v) {
+          const int rr = m0 + r;
+          if (rr >= b) return;
+          double cb[16];
 #pragma unroll
-            for (int u = 0; u < 16; u++)
-              cb[u] = (rr < b && col + u < nn) ? ldg(Cb + rr + (size_t)(n0 + col + u) * b) : 0.0;
-          },
-          [&](int r, int col, const float* v, const double* cb) {
-            const int rr = m0 + r;
-            if (rr >= b) return;
+          for (int u = 0; u < 16; u++) cb[u] = (col + u < nn) ? ldg(Cb + rr + (size_t)(n0 + col + u) * b) : 0.0;
 #pragma unroll
-            for (int u = 0; u < 16; u++)
-              if (col + u < nn) Cb[rr + (size_t)(n0 + col + u) * b] = cb[u] - cvt<double>(v[u]);
-          });
+          for (int u = 0; u < 16; u++)
+            if (col + u < nn) Cb[rr + (size_t)(n0 + col + u) * b] = cb[u] - cvt<double>(v[u]);
+        });
+      } else {
+        tc_epilogue16_pf<double>(
+            tc, 0, nn16,
+            [&](int r, int col, double* cb) {
+              const int rr = m0 + r;
+#pragma unroll
+              for (int u = 0; u < 16; u++)
+                cb[u] = (rr < b && col + u < nn) ? ldg(Cb + rr + (size_t)(n0 + col + u) * b) : 0.0;
+            },
+            [&](int r, int col, const float* v, const double* cb) {
+              const int rr = m0 + r;
+              if (rr >= b) return;
+#pragma unroll
+              for (int u = 0; u < 16; u++)
+                if (col + u < nn) Cb[rr + (size_t)(n0 + col + u) * b] = cb[u] - cvt<double>(v[u]);
+            });
+      }
       PH_END(14);
       }
     }
@@ -1168,7 +1253,7 @@ __device__ void tpmqrt_tc_dense(TaskEnv& env, const double* Yt, const double* Ti
     Ad = env.alloc((size_t)b * b);
     PH(15, tc_densify(env, At, rA, Ad, c));
   }
-  if (prep) tc_apply_prepared(env, prep, Rd, Ad, c);
+  if (prep) tc_apply_prepared<BLR_TC_UPDATE_VARIANT>(env, prep, Rd, Ad, c);
   else tc_apply_ts_dense(env, Yt, Tik, Rd, b, Ad, b, b, c);
   if (rR >= 0) copy_mat(Rt, b, Rd, b, b, b);
   if (rA >= 0) copy_mat(At, b, Ad, b, b, b);

@@ -579,6 +579,36 @@ __device__ __forceinline__ void tc_canon_put16(float* hi, float* lo, int R, int 
   }
 }
 
+// tc_canon for a source whose K index is contiguous (element (r, k) at
+// src[r * sr + k]): a warp takes a tile of 32 consecutive k (one per lane)
+// by 16 rows, so that each of its 16 loads reads 32 consecutive elements,
+// and stores the tile through the four-lane exchange of tc_canon_put16 as
+// 16-byte runs.  Padding rows and columns are written as zeros.
+// exchange: stores through tc_canon_put16 (16-byte runs) or one element
+// at a time (tc_canon_put).
+template <class G>
+__device__ void tc_canon_kmajor(float* hi, float* lo, int R, int K, const G* src, long long sr, int nrow,
+                                int kvalid, bool exchange) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int tk = K / 32, tiles = tk * ((R + 15) / 16);
+  for (int t = warp; t < tiles; t += BLR_NWARP) {
+    const int k = (t % tk) * 32 + lane, r0 = (t / tk) * 16;
+    float v[16];
+    G g[16];
+#pragma unroll
+    for (int u = 0; u < 16; u++) g[u] = (r0 + u < nrow && k < kvalid) ? tc_ld(src + (long long)(r0 + u) * sr + k) : G(0);
+#pragma unroll
+    for (int u = 0; u < 16; u++) v[u] = cvt<float>(g[u]);
+    if (exchange) {
+      tc_canon_put16(hi, lo, R, r0, k, v, R - r0, true);
+    } else {
+#pragma unroll
+      for (int u = 0; u < 16; u++)
+        if (r0 + u < R) tc_canon_put(hi, lo, R, r0 + u, k, v[u]);
+    }
+  }
+}
+
 // Reads the TC_M x ncol accumulator at TMEM columns [col0, col0 + ncol)
 // and calls f(row, col, value) for every element (each once).  Warps w and
 // w + 4 share TMEM lanes 32 (w % 4) .. + 31 and split the columns.

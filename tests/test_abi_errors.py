@@ -189,6 +189,14 @@ def test_solve_entry_points_reject_null_handles(L):
     assert L.blr_trace_export(fake, None, 4, None) == -1
 
 
+def test_tc_update_bench_rejects_on_host(L):
+    ms = ctypes.c_double()
+    assert L.blr_tc_update_bench(96, 1, 1, 0, ctypes.byref(ms), None) == INVALID     # b not a multiple of 128
+    assert L.blr_tc_update_bench(512, 0, 1, 0, ctypes.byref(ms), None) == INVALID    # no CTA
+    assert L.blr_tc_update_bench(512, 1, 1, 5, ctypes.byref(ms), None) == INVALID    # variant not built
+    assert L.blr_tc_update_bench(512, 1, 1, 0, None, None) == INVALID
+
+
 def test_tc_selftest_rejects_on_host(L):
     fake = _P(0x1000)
     assert L.blr_tc_gemm_selftest(None, 128, fake, 8, fake, 128, 128, 8, 8, None) == INVALID
