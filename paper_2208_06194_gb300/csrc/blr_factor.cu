@@ -68,12 +68,12 @@ static int plan_build(blr_factor* const* fs, int count, const blr_opts* o, blr_b
     int p, q, b, nt;
     std::vector<int> offL, offS, offP;
     std::vector<long long> toff;
-    size_t o_offL, o_offS, o_offP, o_toff, slot_of_off;
+    size_t o_offL, o_offS, o_offP, o_toff, slot_of_off, chain_off;
     int base;
   };
   std::vector<Mat> M(count);
   int total = 0, bmax = 0;
-  size_t slot_floats = 0, nt_total = 0;
+  size_t slot_floats = 0, nt_total = 0, q_total = 0;
   for (int m = 0; m < count; m++) {
     const blr_matrix& A = fs[m]->a;
     Mat& x = M[m];
@@ -85,6 +85,8 @@ static int plan_build(blr_factor* const* fs, int count, const blr_opts* o, blr_b
     long long acc = 0;
     for (int k = 0; k < x.q; k++) { x.toff[k] = acc; acc += x.p - k; }
     bmax = std::max(bmax, x.b);
+    x.chain_off = q_total;
+    q_total += (size_t)x.q;
     x.slot_of_off = nt_total;
     nt_total += (size_t)x.nt;
     slot_floats = std::max(slot_floats, (size_t)6 * ((x.b + 127) / 128 * 128) * x.b);
@@ -119,7 +121,8 @@ static int plan_build(blr_factor* const* fs, int count, const blr_opts* o, blr_b
                o_flops = take(sizeof(double) * 4), o_ntask = take(sizeof(unsigned long long) * 4),
                o_tns = take(sizeof(unsigned long long) * 4), o_nvar = take(sizeof(unsigned long long) * 8),
                o_tvar = take(sizeof(unsigned long long) * 8), o_fvar = take(sizeof(double) * 8),
-               o_peak = take(sizeof(unsigned long long)), o_tracen = take(sizeof(unsigned int));
+               o_peak = take(sizeof(unsigned long long)), o_tracen = take(sizeof(unsigned int)),
+               o_chain = take(sizeof(int) * q_total);
   pl->dyn_bytes = bytes - pl->dyn_off;
   const int nsm = blr_num_sms();
   pl->ctas = o->sched_ctas > 0 ? o->sched_ctas : nsm;
@@ -227,6 +230,7 @@ static int plan_build(blr_factor* const* fs, int count, const blr_opts* o, blr_b
     }
     Q.task_base = M[m].base;
     Q.mat_index = m;
+    Q.chain = reinterpret_cast<int*>(base + o_chain) + M[m].chain_off;
     mbase[m] = M[m].base;
     seed[m] = M[m].base;   // GEQRT(0) of every matrix is ready at the start
     rc = blr_cuda_check(cudaMemcpy(base + M[m].o_offL, M[m].offL.data(), sizeof(int) * (M[m].q + 1), cudaMemcpyHostToDevice), "copy offsets");

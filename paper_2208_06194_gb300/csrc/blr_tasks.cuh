@@ -58,7 +58,7 @@
 // The variant of the dense prepared update the factorization runs (see
 // tc_apply_prepared; chosen by measurement with blr_tc_update_bench).
 #ifndef BLR_TC_UPDATE_VARIANT
-#define BLR_TC_UPDATE_VARIANT 0
+#define BLR_TC_UPDATE_VARIANT 1
 #endif
 
 namespace {
@@ -747,6 +747,56 @@ __device__ void tc_apply_lr_prepared(TaskEnv& env, const float* slot, int ry, fl
 // TSQRT(i,k): QR([R_kk; A^V_ik]) with A^V = V^T (low-rank) or the dense tile
 // (Section 3.4.3, Eqs. 19-21); Y_ik overwrites A^V in place.  The panel
 // factorization is FP64; the update of the trailing columns runs in S.
+// The update QRs TSQRT(k+1,k), TSQRT(k+2,k), ... of column k form a chain
+// through R_kk, but each 128-column group of a TSQRT touches only the rows
+// of R_kk of that group, which are final once the previous TSQRT of the
+// chain has finished the same group.  So a TSQRT releases its successor
+// after its first group and publishes its progress in chain[k] as
+// (i - k - 1) G + (groups done), G groups per tile; the successor waits
+// for each group before it starts it (bounded by the watchdog).
+__device__ __forceinline__ int chain_groups(int b) { return (b + 127) / 128; }
+
+// All threads: waits until *flag >= target.  False when the wait ran out
+// (ST_TIMEOUT set) or another error stopped the factorization.
+__device__ bool chain_wait(const SchedParams& P, const int* flag, int target) {
+  __shared__ int ok_sh;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const unsigned long long t0 = tc_gtimer();
+    int ok = 1;
+    while (*(volatile const int*)flag < target) {
+      if (*(volatile int*)P.status != 0) { ok = 0; break; }
+      if (tc_gtimer() - t0 > (unsigned long long)P.watchdog_ns) {
+        atomicOr(P.status, ST_TIMEOUT);
+        ok = 0;
+        break;
+      }
+      __nanosleep(128);
+    }
+    __threadfence();
+    ok_sh = ok;
+  }
+  __syncthreads();
+  return ok_sh != 0;
+}
+
+// All threads: group g of TSQRT(i,k) is done; the first group also releases
+// the next TSQRT of the chain.
+__device__ void chain_publish(TaskEnv& env, int i, int k, int g) {
+  const SchedParams& P = *env.P;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    atomicExch(P.chain + k, (i - k - 1) * chain_groups(P.b) + g + 1);
+    if (g == 0 && i + 1 < P.p && env.skip_succ < 0 && P.task_base + dag_id_tsqrt(*env.dag, i, k) != P.withhold) {
+      const int sid = dag_id_tsqrt(*env.dag, i + 1, k);
+      release_task(P, *env.dag, sid);
+      env.skip_succ = sid;
+    }
+  }
+  __syncthreads();
+}
+
 template <class S>
 __device__ void task_tsqrt(TaskEnv& env, int i, int k, Ctx& c) {
   const SchedParams& P = *env.P;
@@ -757,9 +807,18 @@ __device__ void task_tsqrt(TaskEnv& env, int i, int k, Ctx& c) {
   double* B = tile_ptr(P, i, k);
   const int ry = (r < 0) ? b : r;
   View<double> Bv = (r < 0) ? colmajor(B, b) : rowmajor(B + (size_t)b * P.cap, b);
+  const int ng = chain_groups(b);
+  const int pred_base = (i - k - 2) * ng;     // progress of TSQRT(i-1,k) before its group 0
+  const bool has_pred = P.chain != nullptr && i > k + 1;
   if (ry == 0) {
+    // a rank-0 tail leaves R_kk as it is: wait for the predecessor to finish
+    // it, then pass it on as done
     for (int e = threadIdx.x; e < BLR_NB * b; e += BLR_NT) Tk[e] = 0.0;
     __syncthreads();
+    if (P.chain) {
+      if (has_pred && !chain_wait(P, P.chain + k, pred_base + ng)) return;
+      chain_publish(env, i, k, ng - 1);
+    }
     return;
   }
   // mixed path, dense tail: the panels' updates reach only the columns of
@@ -776,6 +835,9 @@ __device__ void task_tsqrt(TaskEnv& env, int i, int k, Ctx& c) {
     const int w = BLR_NB;
     const int ldb = ry | 1;
     const int gend = grouped ? min(b, (c0 / 128 + 1) * 128) : b;   // end of this panel's update range
+    // the rows of R_kk of this group are final once the previous update QR
+    // of the chain has finished the group
+    if (has_pred && c0 % 128 == 0 && !chain_wait(P, P.chain + k, pred_base + c0 / 128 + 1)) return;
     __syncthreads();
     for (int e = threadIdx.x; e < w * w; e += BLR_NT) {
       int a = e % w, l = e / w;
@@ -813,6 +875,7 @@ __device__ void task_tsqrt(TaskEnv& env, int i, int k, Ctx& c) {
       PH(20, tc_apply_ts_group(env, B + (size_t)g0 * b, b, 128, Tk + (size_t)g0 * BLR_NB, R + g0 + (size_t)gend * b,
                                b, B + (size_t)gend * b, b, b - gend, gTg, gZs, c));
     }
+    if (P.chain && ((c0 + w) % 128 == 0 || c0 + w == b)) chain_publish(env, i, k, c0 / 128);
   }
   if constexpr (std::is_same<S, float>::value) {
     if (r != 0 && P.prep && env.tc && k + 1 < P.q) {
@@ -823,7 +886,7 @@ __device__ void task_tsqrt(TaskEnv& env, int i, int k, Ctx& c) {
       __threadfence();
       __syncthreads();
       if (threadIdx.x == 0) {
-        if (i + 1 < P.p && P.task_base + dag_id_tsqrt(*env.dag, i, k) != P.withhold) {
+        if (i + 1 < P.p && env.skip_succ < 0 && P.task_base + dag_id_tsqrt(*env.dag, i, k) != P.withhold) {
           const int sid = dag_id_tsqrt(*env.dag, i + 1, k);
           release_task(P, *env.dag, sid);
           env.skip_succ = sid;

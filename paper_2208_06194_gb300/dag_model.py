@@ -19,11 +19,12 @@ Algorithm 4, with the edges the scheduler releases (``csrc/blr_dag.h``):
     TSQRT(i, k)   -> TSQRT(i+1, k), TPMQRT(i, j, k) for j > k
     TPMQRT(i,j,k) -> TPMQRT(i+1, j, k), and the step-(k+1) task on tile (i, j)
 
-Indices are 0-based (k < q, i in (k, p), j in (k, q)).  A TSQRT may release
-its successor TSQRT before it ends: the mixed path does so once its FP64
-panel is done and before it prepares its updates' tensor-core operands.
-``chain`` is the fraction of a TSQRT's time after which that happens (1.0:
-at its end, as on the FP64 path).
+Indices are 0-based (k < q, i in (k, p), j in (k, q)).  A TSQRT releases
+its successor TSQRT before it ends: after its first 128-column group, the
+successor then running each group once the predecessor has finished it
+(update-QR chain pipelining), so the chain advances by about one group's
+time per TSQRT.  ``chain`` is the fraction of a TSQRT's time after which
+the successor can proceed (1.0: at its end, no pipelining).
 
 Usage: ``python -m paper_2208_06194_gb300.dag_model --p 128 --q 64
 --workers 152 --geqrt 15e-3 --larfb 13e-3 --tsqrt 18e-3 --tpmqrt 1.68e-3

@@ -58,8 +58,9 @@ def test_watchdog_ends_a_stalled_scheduler(lib, prec, withheld):
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
 def test_trace_records_every_task_in_dependency_order(lib, prec):
     """opts.trace: one event per task, the task set equals the DAG's, and no
-    task starts before a predecessor ended (the mixed path releases the next
-    update QR of a column before its own end, so that edge is exempt)."""
+    task starts before a predecessor ended (an update QR releases the next
+    one of its column after its first 128-column group, so that edge is
+    exempt; the next one starts after it did)."""
     ref, make = _small(lib, seed=33)
     p, q = 8, 4
     precision = lib.BLR_PREC_MIXED if prec == "mixed" else lib.BLR_PREC_FP64
@@ -77,7 +78,8 @@ def test_trace_records_every_task_in_dependency_order(lib, prec):
         assert e["t_end_ns"] >= e["t_start_ns"] and 0 <= e["cta"] and e["matrix"] == 0
         for sid in lib.blr_dag_task(p, q, t)[1]:
             s = got[lib.blr_dag_task(p, q, sid)[0]]
-            if prec == "mixed" and key[0] == 2 and s["type"] == 2:
+            if key[0] == 2 and s["type"] == 2:
+                assert s["t_start_ns"] >= e["t_start_ns"], (key, s)
                 continue
             assert s["t_start_ns"] >= e["t_end_ns"], (key, s)
     ct = lib.chrome_trace(events)
