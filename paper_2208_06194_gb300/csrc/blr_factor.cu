@@ -73,7 +73,7 @@ static int plan_build(blr_factor* const* fs, int count, const blr_opts* o, blr_b
   };
   std::vector<Mat> M(count);
   int total = 0, bmax = 0;
-  size_t slot_floats = 0, nt_total = 0, q_total = 0;
+  size_t slot_floats = 0, nt_total = 0, chain_total = 0;
   for (int m = 0; m < count; m++) {
     const blr_matrix& A = fs[m]->a;
     Mat& x = M[m];
@@ -85,8 +85,8 @@ static int plan_build(blr_factor* const* fs, int count, const blr_opts* o, blr_b
     long long acc = 0;
     for (int k = 0; k < x.q; k++) { x.toff[k] = acc; acc += x.p - k; }
     bmax = std::max(bmax, x.b);
-    x.chain_off = q_total;
-    q_total += (size_t)x.q;
+    x.chain_off = chain_total;
+    chain_total += (size_t)x.nt;
     x.slot_of_off = nt_total;
     nt_total += (size_t)x.nt;
     slot_floats = std::max(slot_floats, (size_t)6 * ((x.b + 127) / 128 * 128) * x.b);
@@ -122,7 +122,7 @@ static int plan_build(blr_factor* const* fs, int count, const blr_opts* o, blr_b
                o_tns = take(sizeof(unsigned long long) * 4), o_nvar = take(sizeof(unsigned long long) * 8),
                o_tvar = take(sizeof(unsigned long long) * 8), o_fvar = take(sizeof(double) * 8),
                o_peak = take(sizeof(unsigned long long)), o_tracen = take(sizeof(unsigned int)),
-               o_chain = take(sizeof(int) * q_total);
+               o_chain = take(sizeof(int) * chain_total);
   pl->dyn_bytes = bytes - pl->dyn_off;
   const int nsm = blr_num_sms();
   pl->ctas = o->sched_ctas > 0 ? o->sched_ctas : nsm;

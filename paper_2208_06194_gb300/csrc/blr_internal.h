@@ -128,7 +128,7 @@ struct SchedParams {
   int trace_cap;
   unsigned int* trace_n;
   int withhold;                  // test hook: batch-wide id of a task that releases nothing, or -1
-  int* chain;                    // per block column k: progress of its update-QR chain (reset per launch)
+  int* chain;                    // per reflector block (toff[k] + i - k): groups done by TSQRT(i,k) (reset per launch)
 };
 
 // host helpers (blr_api.cu)

@@ -751,9 +751,12 @@ __device__ void tc_apply_lr_prepared(TaskEnv& env, const float* slot, int ry, fl
 // through R_kk, but each 128-column group of a TSQRT touches only the rows
 // of R_kk of that group, which are final once the previous TSQRT of the
 // chain has finished the same group.  So a TSQRT releases its successor
-// after its first group and publishes its progress in chain[k] as
-// (i - k - 1) G + (groups done), G groups per tile; the successor waits
-// for each group before it starts it (bounded by the watchdog).
+// after its first group and publishes the number of groups it has done in
+// chain[toff[k] + i - k] (one counter per update QR, written by it alone,
+// so it only grows); the successor waits for each group before it starts
+// it (bounded by the watchdog).  One shared counter per column would not
+// do: a slower predecessor's later write could lower it under a waiter's
+// target for good.
 __device__ __forceinline__ int chain_groups(int b) { return (b + 127) / 128; }
 
 // All threads: waits until *flag >= target.  False when the wait ran out
@@ -787,7 +790,7 @@ __device__ void chain_publish(TaskEnv& env, int i, int k, int g) {
   __threadfence();
   __syncthreads();
   if (threadIdx.x == 0) {
-    atomicExch(P.chain + k, (i - k - 1) * chain_groups(P.b) + g + 1);
+    atomicExch(P.chain + P.toff_dev[k] + (i - k), g + 1);
     if (g == 0 && i + 1 < P.p && env.skip_succ < 0 && P.task_base + dag_id_tsqrt(*env.dag, i, k) != P.withhold) {
       const int sid = dag_id_tsqrt(*env.dag, i + 1, k);
       release_task(P, *env.dag, sid);
@@ -808,15 +811,15 @@ __device__ void task_tsqrt(TaskEnv& env, int i, int k, Ctx& c) {
   const int ry = (r < 0) ? b : r;
   View<double> Bv = (r < 0) ? colmajor(B, b) : rowmajor(B + (size_t)b * P.cap, b);
   const int ng = chain_groups(b);
-  const int pred_base = (i - k - 2) * ng;     // progress of TSQRT(i-1,k) before its group 0
   const bool has_pred = P.chain != nullptr && i > k + 1;
+  const int* pred = has_pred ? P.chain + P.toff_dev[k] + (i - 1 - k) : nullptr;   // TSQRT(i-1,k)'s groups done
   if (ry == 0) {
     // a rank-0 tail leaves R_kk as it is: wait for the predecessor to finish
     // it, then pass it on as done
     for (int e = threadIdx.x; e < BLR_NB * b; e += BLR_NT) Tk[e] = 0.0;
     __syncthreads();
     if (P.chain) {
-      if (has_pred && !chain_wait(P, P.chain + k, pred_base + ng)) return;
+      if (has_pred && !chain_wait(P, pred, ng)) return;
       chain_publish(env, i, k, ng - 1);
     }
     return;
@@ -837,7 +840,7 @@ __device__ void task_tsqrt(TaskEnv& env, int i, int k, Ctx& c) {
     const int gend = grouped ? min(b, (c0 / 128 + 1) * 128) : b;   // end of this panel's update range
     // the rows of R_kk of this group are final once the previous update QR
     // of the chain has finished the group
-    if (has_pred && c0 % 128 == 0 && !chain_wait(P, P.chain + k, pred_base + c0 / 128 + 1)) return;
+    if (has_pred && c0 % 128 == 0 && !chain_wait(P, pred, c0 / 128 + 1)) return;
     __syncthreads();
     for (int e = threadIdx.x; e < w * w; e += BLR_NT) {
       int a = e % w, l = e / w;
