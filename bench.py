@@ -687,6 +687,7 @@ def main():
         "ranks": {"before": {"n_dense": st_a["n_dense"], "mean": st_a["mean_rank"], "max": st_a["max_rank"]},
                   "after": {"n_dense": st["n_dense"], "mean": st["mean_rank"], "max": st["max_rank"]}},
         "kernel_seconds": k_sec,
+        "prep_pool": {"slots": st.get("prep_slots"), "misses": st.get("prep_misses")},
         "task_cta_seconds": dict(zip(["geqrt", "larfb", "tsqrt", "tpmqrt"], st["task_seconds"])),
         "tpmqrt_kinds": tpmqrt_kinds(st, prec == blr.BLR_PREC_FP64),
         "dense_equivalent": dense_equivalent(s["m"], s["n"], t_step),
