@@ -52,11 +52,15 @@ TRAFFIC_FILE = os.path.join(ROOT, "profiles", "k_factor_mixed_traffic_yukawa3d.m
 
 
 def csrc_digest() -> str:
-    """sha256 (16 hex digits) of the CUDA sources of the library."""
+    """sha256 (16 hex digits) of the CUDA sources the factorization kernel is
+    built from: every file of csrc/ but blr_solve.cu, which holds only the
+    kernels that use a finished factor (Q application, solves, products)."""
     import hashlib
     h = hashlib.sha256()
     d = os.path.join(ROOT, "paper_2208_06194_gb300", "csrc")
     for name in sorted(os.listdir(d)):
+        if name == "blr_solve.cu":
+            continue
         with open(os.path.join(d, name), "rb") as fh:
             h.update(name.encode() + b"\0" + fh.read())
     return h.hexdigest()[:16]

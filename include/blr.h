@@ -452,8 +452,8 @@ int blr_tc_gemm_selftest(const double* a_dev, int lda, const double* b_dev, int 
  * CTAs each repeat the update reps times on their own b x b tiles with one
  * shared slot of prepared operands, filled with synthetic bounded values.
  * variant selects an implementation variant of its conversion and
- * epilogues (0, 1, 2, 3, 4, 6, 9, 11 or 15; 1 is the factorization's, the
- * fastest measured at b = 512 on 152 CTAs).
+ * epilogues and its tile order (0, 1, 2, 3, 4, 6, 9, 11, 15, 17 or 19; the
+ * factorization uses the fastest measured at b = 512 on 152 CTAs).
  * *ms_per_update (host) receives the mean device time of one update per
  * CTA; *aggregate_tflops (host, may be NULL) the algorithmic rate of the
  * whole launch.  Errors: BLR_ERR_INVALID (b not a multiple of 128 in

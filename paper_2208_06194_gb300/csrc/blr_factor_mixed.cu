@@ -117,11 +117,11 @@ extern "C" int blr_tc_update_bench(int b, int ctas, int reps, int variant, doubl
     blr_set_error("blr_tc_update_bench: b must be a multiple of 128 in [128, %d], ctas and reps >= 1", BLR_BMAX);
     return BLR_ERR_INVALID;
   }
-  static const int kVariants[] = {0, 1, 2, 3, 4, 6, 9, 11, 15};
+  static const int kVariants[] = {0, 1, 2, 3, 4, 6, 9, 11, 15, 17, 19};
   bool known = false;
   for (int v : kVariants) known = known || v == variant;
   if (!known) {
-    blr_set_error("blr_tc_update_bench: variant %d not built (0, 1, 2, 3, 4, 6, 9, 11, 15)", variant);
+    blr_set_error("blr_tc_update_bench: variant %d not built (0, 1, 2, 3, 4, 6, 9, 11, 15, 17, 19)", variant);
     return BLR_ERR_INVALID;
   }
   const int Rp = b;
@@ -168,7 +168,9 @@ extern "C" int blr_tc_update_bench(int b, int ctas, int reps, int variant, doubl
       case 6: rc = launch_update_bench<6>(P, ctas, ct, cb, slot, reps, ns, 0); break;
       case 9: rc = launch_update_bench<9>(P, ctas, ct, cb, slot, reps, ns, 0); break;
       case 11: rc = launch_update_bench<11>(P, ctas, ct, cb, slot, reps, ns, 0); break;
-      default: rc = launch_update_bench<15>(P, ctas, ct, cb, slot, reps, ns, 0); break;
+      case 15: rc = launch_update_bench<15>(P, ctas, ct, cb, slot, reps, ns, 0); break;
+      case 17: rc = launch_update_bench<17>(P, ctas, ct, cb, slot, reps, ns, 0); break;
+      default: rc = launch_update_bench<19>(P, ctas, ct, cb, slot, reps, ns, 0); break;
     }
     if (rc) break;
     cudaEventRecord(e1);

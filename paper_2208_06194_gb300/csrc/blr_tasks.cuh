@@ -58,7 +58,7 @@
 // The variant of the dense prepared update the factorization runs (see
 // tc_apply_prepared; chosen by measurement with blr_tc_update_bench).
 #ifndef BLR_TC_UPDATE_VARIANT
-#define BLR_TC_UPDATE_VARIANT 1
+#define BLR_TC_UPDATE_VARIANT 17
 #endif
 
 namespace {
@@ -484,7 +484,8 @@ __device__ void tsqrt_prep(TaskEnv& env, int i, int k, float* slot, Ctx& c) {
 // converted by K-major tiles with coalesced loads; bit 3 with it, those
 // tiles are stored through the four-lane exchange; bit 1, the epilogues
 // issue their FP64 loads before reading TMEM; bit 2, the Z and W operands
-// are stored through the four-lane exchange.
+// are stored through the four-lane exchange; bit 4, the output tiles are
+// visited column block by column block (row tiles innermost).
 template <int V = 0>
 __device__ void tc_apply_prepared(TaskEnv& env, const float* slot, double* Ct, double* Cb, Ctx& c) {
   const SchedParams& P = *env.P;
@@ -506,9 +507,15 @@ __device__ void tc_apply_prepared(TaskEnv& env, const float* slot, double* Ct, d
   fence_async_global();
   __syncthreads();
   const int nchunk = b / TC_KC;
+  // output tiles of TC_M rows x 256 columns; bit 4 of V runs the row tiles
+  // innermost, so that consecutive products share their B operand
+  const int mt = (b + TC_M - 1) / TC_M, nt = (b + 255) / 256, ntile = mt * nt;
+  auto tile_m0 = [&](int t) { return ((V & 16) != 0 ? t % mt : t / nt) * TC_M; };
+  auto tile_n0 = [&](int t) { return ((V & 16) != 0 ? t / mt : t % nt) * 256; };
   // Z = Ct + Y^T Cb
-  for (int m0 = 0; m0 < b; m0 += TC_M) {
-    for (int n0 = 0; n0 < b; n0 += 256) {
+  for (int t = 0; t < ntile; t++) {
+    {
+      const int m0 = tile_m0(t), n0 = tile_n0(t);
       const int nn = min(256, b - n0), nn16 = (nn + 15) & ~15;
       PH(13, tc_gemm_bulk(tc, q, 0, yt_h + (size_t)m0 * TC_KC, yt_l + (size_t)m0 * TC_KC, cs, cc_h + (size_t)n0 * TC_KC,
                    cc_l + (size_t)n0 * TC_KC, cs, nn16, nchunk));
@@ -555,9 +562,10 @@ __device__ void tc_apply_prepared(TaskEnv& env, const float* slot, double* Ct, d
   fence_async_global();
   __syncthreads();
   // W = T^T Z (T^T lower triangular: rows m0.. need K < m0 + 128); Ct -= W
-  for (int m0 = 0; m0 < b; m0 += TC_M) {
-    const int kch = min(b, m0 + TC_M) / TC_KC;
-    for (int n0 = 0; n0 < b; n0 += 256) {
+  for (int t = 0; t < ntile; t++) {
+    {
+      const int m0 = tile_m0(t), n0 = tile_n0(t);
+      const int kch = min(b, m0 + TC_M) / TC_KC;
       const int nn = min(256, b - n0), nn16 = (nn + 15) & ~15;
       PH(13, tc_gemm_bulk(tc, q, 0, tt_h + (size_t)m0 * TC_KC, tt_l + (size_t)m0 * TC_KC, cs, zc_h + (size_t)n0 * TC_KC,
                    zc_l + (size_t)n0 * TC_KC, cs, nn16, kch));
@@ -610,8 +618,9 @@ __device__ void tc_apply_prepared(TaskEnv& env, const float* slot, double* Ct, d
   fence_async_global();
   __syncthreads();
   // Cb -= Y W
-  for (int m0 = 0; m0 < b; m0 += TC_M) {
-    for (int n0 = 0; n0 < b; n0 += 256) {
+  for (int t = 0; t < ntile; t++) {
+    {
+      const int m0 = tile_m0(t), n0 = tile_n0(t);
       const int nn = min(256, b - n0), nn16 = (nn + 15) & ~15;
       PH(13, tc_gemm_bulk(tc, q, 0, yc_h + (size_t)m0 * TC_KC, yc_l + (size_t)m0 * TC_KC, cs, cc_h + (size_t)n0 * TC_KC,
                    cc_l + (size_t)n0 * TC_KC, cs, nn16, nchunk));
