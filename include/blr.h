@@ -281,6 +281,13 @@ void blr_batch_plan_destroy(blr_batch_plan* plan);
  * trans = 0: B <- Q^T B (reflectors in factorization order);
  * trans = 1: B <- Q B (reverse order; Algorithm 5 read with the "I -" of
  * Eq. 21's reflector).  Exact application of the stored reflectors.
+ * Columns run in groups of 16; the b/32 blocks of 32 reflectors of each
+ * update QR are applied by b/32 CTAs as a pipeline that keeps Algorithm
+ * 5's order on every block row, as many groups per launch as the SMs hold
+ * at once.  Its CTAs wait on one another with a bounded wait: a wait that
+ * runs out (only if the GPU cannot keep all of a launch's CTAs resident)
+ * ends the call with BLR_ERR_TIMEOUT.  Errors: BLR_ERR_INVALID, BLR_ERR_OOM,
+ * BLR_ERR_CUDA, BLR_ERR_TIMEOUT.
  */
 int blr_apply_qt(const blr_factor* f, double* b_dev, int ldb, int nrhs, int trans,
                  void* stream);

@@ -4,6 +4,7 @@
 // least squares, Section 1) and its adjoint.  Every kernel gives each CTA a
 // group of right-hand-side columns; the reflector sequence is applied in
 // order inside the CTA.
+#include <algorithm>
 #include <mutex>
 #include <cstdio>
 #include <vector>
@@ -80,6 +81,159 @@ __global__ void __launch_bounds__(BLR_NT, 1) k_apply_q(FactorView F, double* B, 
       for (int i = F.p - 1; i > k; i--)
         apply_ts_tile(F, i, k, Bc + (size_t)k * b, Bc + (size_t)i * b, ldb, nc, false, scr, c);
       apply_q<double>(ftile(F, k, k), b, b, b, ft(F, k, k), Bc + (size_t)k * b, ldb, nc, false, c);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Q^T B and Q B as a pipeline over the 32-reflector blocks of each update QR.
+// k_apply_q gives one CTA a group of columns and walks every reflector in
+// order, so a few right-hand sides use a few SMs.  Here the S = b/32
+// reflector blocks of each TSQRT(i,k) are split over S CTAs: CTA s applies
+// block s of every TSQRT, which touches rows [32 s, 32 s + 32) of B_k and
+// all of B_i.  Rows of B_k stay with one CTA; the order of the steps on each
+// B_i is kept by a counter per (column group, i) that counts the steps done
+// on it as the lower block (the order of Algorithm 5: column k ascending,
+// then i, then block s; reversed for Q B), and a flag per k marks the
+// diagonal block's reflectors (GEQRT(k)) as applied.  A step waits until its
+// B_i counter reaches the number of steps on B_i that precede it, so the
+// CTAs run as a wavefront down the columns with up to S steps in flight.
+// Each element sees exactly the arithmetic of k_apply_q.  A low-rank
+// reflector block acts on P = U_ik^T B_i (Eqs. 19-21): its first step forms
+// P and P0 = P in a buffer per (group, i), the others update P, the last
+// adds U (P - P0) to B_i.  Waits are bounded (the status gets ST_TIMEOUT).
+// ---------------------------------------------------------------------------
+struct WaveState {
+  int* prog;       // [groups][p]: steps done on B_i as the lower block
+  int* geq;        // [groups][q]: 1 once GEQRT(k)'s reflectors are applied to B_k
+  double* pbuf;    // [groups][p][2 cap cpc]: P and P0 of a low-rank step
+  unsigned long long limit_ns;
+};
+
+__device__ __forceinline__ unsigned long long wave_timer() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Thread 0 waits until *flag >= target; every thread returns whether it got
+// there (false after the limit or once another CTA has timed out).
+__device__ bool wave_wait(const int* flag, int target, const WaveState& W, int* status) {
+  __shared__ int ok_sh;
+  if (threadIdx.x == 0) {
+    int ok = 1;
+    const unsigned long long t0 = wave_timer();
+    while (*(volatile const int*)flag < target) {
+      if ((*(volatile int*)status & ST_TIMEOUT) || wave_timer() - t0 > W.limit_ns) {
+        atomicOr(status, ST_TIMEOUT);
+        ok = 0;
+        break;
+      }
+      __nanosleep(200);
+    }
+    __threadfence();
+    ok_sh = ok;
+  }
+  __syncthreads();
+  return ok_sh != 0;
+}
+
+// Makes this CTA's global writes visible, then sets *flag = value.
+__device__ void wave_publish(int* flag, int value) {
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) atomicExch(flag, value);
+}
+
+// Step (i, k, s): reflector block s of TSQRT(i,k) on [B_k rows 32 s..; B_i].
+__device__ void wave_step(const FactorView& F, int i, int k, int s, double* Bk, double* Bi, long long ldb, int nc,
+                          bool trans, double* pb, int cpc, Ctx& c) {
+  const int b = F.b, S = b / BLR_NB;
+  const int r = __ldcg(F.rank + (size_t)k * F.p + i);
+  if (r == 0) return;
+  const double* Y = ftile(F, i, k);
+  const double* T = ft(F, i, k);
+  const int c0 = s * BLR_NB;
+  if (r < 0) {
+    const int ldy = stage_reflector_panel<double>(colmajor(const_cast<double*>(Y), b), b, c0, BLR_NB, T, c);
+    apply_refl_ts(Bk + c0, ldb, colmajor(Bi, (int)ldb), b, nc, (const double*)as<double>(c.s.pnl), ldy, BLR_NB,
+                  (const double*)as<double>(c.s.t), trans, c);
+    return;
+  }
+  double* Pm = pb;
+  double* P0 = pb + (size_t)F.cap * cpc;
+  const bool first = trans ? s == 0 : s == S - 1, last = trans ? s == S - 1 : s == 0;
+  if (first) {
+    gemm(r, nc, b, 1.0, Y, b, true, Bi, ldb, false, 0.0, Pm, r, c);
+    __syncthreads();
+    copy_mat(P0, r, Pm, r, r, nc);
+  }
+  const int ldy = stage_reflector_panel<double>(rowmajor(const_cast<double*>(Y) + (size_t)b * F.cap, b), r, c0,
+                                                BLR_NB, T, c);
+  apply_refl_ts(Bk + c0, ldb, colmajor(Pm, r), r, nc, (const double*)as<double>(c.s.pnl), ldy, BLR_NB,
+                (const double*)as<double>(c.s.t), trans, c);
+  if (last) {
+    __syncthreads();
+    for (int e = threadIdx.x; e < r * nc; e += BLR_NT) Pm[e] = ldg(Pm + e) - ldg(P0 + e);
+    __syncthreads();
+    gemm(b, nc, r, 1.0, Y, b, false, Pm, r, false, 1.0, Bi, ldb, c);
+  }
+}
+
+__global__ void __launch_bounds__(BLR_NT, 1) k_apply_q_wave(FactorView F, WaveState W, double* B, long long ldb,
+                                                             int nrhs, int trans, int cpc, int g0) {
+  extern __shared__ double smem[];
+  Ctx c;
+  c.s = sm_carve(smem);
+  c.status = F.status;
+  c.fma = 0.0;
+  const int S = F.b / BLR_NB;
+  const int g = g0 + blockIdx.x / S, s = blockIdx.x % S;
+  const int col0 = g * cpc;
+  const int nc = min(cpc, nrhs - col0);
+  if (nc <= 0) return;
+  double* Bc = B + (size_t)col0 * ldb;
+  int* prog = W.prog + (size_t)g * F.p;
+  int* geq = W.geq + (size_t)g * F.q;
+  double* pbuf = W.pbuf + (size_t)g * F.p * 2 * F.cap * cpc;
+  const size_t pstride = (size_t)2 * F.cap * cpc;
+  const int b = F.b, p = F.p, q = F.q;
+  if (trans) {
+    for (int k = 0; k < q; k++) {
+      double* Bk = Bc + (size_t)k * b;
+      if (s == 0) {
+        if (!wave_wait(prog + k, S * k, W, F.status)) return;
+        apply_q<double>(ftile(F, k, k), b, b, b, ft(F, k, k), Bk, ldb, nc, true, c);
+        wave_publish(geq + k, 1);
+      } else if (!wave_wait(geq + k, 1, W, F.status)) {
+        return;
+      }
+      for (int i = k + 1; i < p; i++) {
+        if (!wave_wait(prog + i, S * k + s, W, F.status)) return;
+        wave_step(F, i, k, s, Bk, Bc + (size_t)i * b, ldb, nc, true, pbuf + i * pstride, cpc, c);
+        wave_publish(prog + i, S * k + s + 1);
+      }
+    }
+  } else {
+    for (int k = q - 1; k >= 0; k--) {
+      double* Bk = Bc + (size_t)k * b;
+      for (int i = p - 1; i > k; i--) {
+        // steps on B_i before this one: blocks S-1 .. s+1 of column k, and
+        // every block of the columns k+1 .. min(i, q)-1 processed before it;
+        // for i < q, GEQRT(i) (processed with column i) comes first too
+        const int target = S * (min(i, q) - 1 - k) + (S - 1 - s);
+        if (i < q && !wave_wait(geq + i, 1, W, F.status)) return;
+        if (!wave_wait(prog + i, target, W, F.status)) return;
+        wave_step(F, i, k, s, Bk, Bc + (size_t)i * b, ldb, nc, false, pbuf + i * pstride, cpc, c);
+        wave_publish(prog + i, target + 1);
+      }
+      if (s == 0) {
+        // block 0 is the last of every step on B_k's rows in this column:
+        // after CTA 0's own step (k+1, k, 0) every other CTA's rows of B_k
+        // are final (they precede it on B_{k+1}'s counter)
+        apply_q<double>(ftile(F, k, k), b, b, b, ft(F, k, k), Bk, ldb, nc, false, c);
+        wave_publish(geq + k, 1);
+      }
     }
   }
 }
@@ -292,10 +446,12 @@ struct Scratch {
   double* scratch = nullptr;
   long long* toff = nullptr;
   int* status = nullptr;
+  int* flags = nullptr;
   ~Scratch() {
     if (scratch) cudaFree(scratch);
     if (toff) cudaFree(toff);
     if (status) cudaFree(status);
+    if (flags) cudaFree(flags);
   }
 };
 
@@ -336,6 +492,10 @@ int finish(const FactorView& F, cudaStream_t st, const char* what) {
     blr_set_error("%s: zero or non-finite diagonal entry of R", what);
     return BLR_ERR_NUMERIC;
   }
+  if (s & ST_TIMEOUT) {
+    blr_set_error("%s: a device wait between CTAs ran out", what);
+    return BLR_ERR_TIMEOUT;
+  }
   return BLR_OK;
 }
 
@@ -356,6 +516,7 @@ int set_smem() {
   std::lock_guard<std::mutex> lock(g_smem_mu);
   if (g_smem_done[dev]) return BLR_OK;
   rc = blr_cuda_check(cudaFuncSetAttribute(k_apply_q, cudaFuncAttributeMaxDynamicSharedMemorySize, BLR_SMEM_BYTES), "smem");
+  if (!rc) rc = blr_cuda_check(cudaFuncSetAttribute(k_apply_q_wave, cudaFuncAttributeMaxDynamicSharedMemorySize, BLR_SMEM_BYTES), "smem");
   if (!rc) rc = blr_cuda_check(cudaFuncSetAttribute(k_solve_r, cudaFuncAttributeMaxDynamicSharedMemorySize, BLR_SMEM_BYTES), "smem");
   if (!rc) rc = blr_cuda_check(cudaFuncSetAttribute(k_matmul, cudaFuncAttributeMaxDynamicSharedMemorySize, BLR_SMEM_BYTES), "smem");
   if (!rc) rc = blr_cuda_check(cudaFuncSetAttribute(k_solve_rt, cudaFuncAttributeMaxDynamicSharedMemorySize, BLR_SMEM_BYTES), "smem");
@@ -364,24 +525,52 @@ int set_smem() {
   return rc;
 }
 
-// Right-hand-side columns per CTA (kColsPerCta).  Each CTA streams every
-// reflector block of the factor for its columns, so the reflector traffic
-// grows with the number of CTAs: measured at 65536 x 32768 with 16
-// right-hand sides, 8 columns per CTA (2 CTAs) took 6 s per Q application,
-// 1 column per CTA (16 CTAs) 23 s.
+// Right-hand-side columns per CTA (kColsPerCta) of the kernels that give
+// each CTA its own columns (k_apply_q of the no-allocation entry, the R
+// solves).  Each CTA streams every block of the factor for its columns, so
+// the traffic grows with the number of CTAs: measured for k_apply_q at
+// 65536 x 32768 with 16 right-hand sides, 8 columns per CTA (2 CTAs) took
+// 6 s per Q application, 1 column per CTA (16 CTAs) 23 s.
 int cols_per_cta(int) { return kColsPerCta; }
 
+// Right-hand-side columns per group of the pipelined Q application: each
+// group's b/32 CTAs read every reflector block once.
+constexpr int kWaveCols = 16;
+// Bound of each wait between the pipeline's CTAs.
+constexpr unsigned long long kWaveLimitNs = 20ull * 1000 * 1000 * 1000;
+
 int apply_q_launch(const blr_factor* f, double* B, int ldb, int nrhs, int trans, cudaStream_t st) {
+  const blr_matrix& a = f->a;
+  const int S = a.b / BLR_NB, cpc = kWaveCols;
+  const int groups = (nrhs + cpc - 1) / cpc;
+  int dev = 0, nsm = 0;
+  int rc = blr_cuda_check(cudaGetDevice(&dev), "cudaGetDevice");
+  if (!rc) rc = blr_cuda_check(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev), "SM count");
+  if (rc) return rc;
+  // the CTAs of a group wait on one another, so every CTA of a launch must
+  // be resident at once: one per SM (the shared-memory footprint), so at
+  // most nsm / S groups per launch, the rest in further launches
+  const int per_launch = std::max(1, nsm / S);
+  if (S > nsm) {
+    blr_set_error("blr_apply_qt: %d reflector blocks per tile exceed the %d SMs", S, nsm);
+    return BLR_ERR_INVALID;
+  }
   FactorView F{};
-  Scratch S;
-  const int cpc = cols_per_cta(nrhs);
-  const int nct = (nrhs + cpc - 1) / cpc;
-  int rc = set_smem();
-  if (!rc) rc = make_view(f->a, f->t, f->a.q, &F, &S, nct, (size_t)2 * f->a.cap * cpc + 64, st);
+  Scratch Sc;
+  rc = set_smem();
+  if (!rc) rc = make_view(a, f->t, a.q, &F, &Sc, 1, (size_t)groups * a.p * 2 * a.cap * cpc + 64, st);
   if (rc) return rc;
-  k_apply_q<<<nct, BLR_NT, BLR_SMEM_BYTES, st>>>(F, B, ldb, nrhs, trans, cpc);
-  rc = blr_cuda_check(cudaGetLastError(), "launch k_apply_q");
+  const size_t nflags = (size_t)groups * (a.p + a.q);
+  rc = blr_cuda_check(cudaMalloc(&Sc.flags, sizeof(int) * nflags), "apply flags");
+  if (!rc) rc = blr_cuda_check(cudaMemsetAsync(Sc.flags, 0, sizeof(int) * nflags, st), "memset");
   if (rc) return rc;
+  WaveState W{Sc.flags, Sc.flags + (size_t)groups * a.p, F.scratch, kWaveLimitNs};
+  for (int g0 = 0; g0 < groups; g0 += per_launch) {
+    const int n = std::min(per_launch, groups - g0);
+    k_apply_q_wave<<<n * S, BLR_NT, BLR_SMEM_BYTES, st>>>(F, W, B, ldb, nrhs, trans, cpc, g0);
+    rc = blr_cuda_check(cudaGetLastError(), "launch k_apply_q_wave");
+    if (rc) return rc;
+  }
   return finish(F, st, "blr_apply_qt");
 }
 

@@ -96,6 +96,29 @@ def test_q_application_parity(lib, m, n, b, seed, dense, zero):
     fac.destroy()
 
 
+@pytest.mark.parametrize("m,n,b,nrhs", [(1024, 512, 128, 700), (2048, 1024, 512, 150), (512, 512, 64, 33)])
+def test_q_application_over_several_column_groups(lib, m, n, b, nrhs):
+    """The pipelined Q application splits each TSQRT's b/32 reflector
+    blocks over as many CTAs and runs 16 right-hand sides per group, as many
+    groups per launch as the SMs hold at once (one CTA per SM).  700 columns
+    at b = 128 (44 groups of 4 CTAs) and 150 at b = 512 (10 groups of 16)
+    take two launches; the square case has no update QR below the last
+    diagonal tile and a ragged last group.  Q^T B and Q B against the
+    oracle, low-rank, dense and zero reflector blocks mixed."""
+    import torch
+    p, q = m // b, n // b
+    a = _mixed_blr(m, n, b, 11 + b, ((p - 1, 0), (2, 1)), ((p - 2, 0),))
+    ref, fac, fo = _factor_both(lib, a, b)
+    c = np.random.default_rng(b + nrhs).standard_normal((m, nrhs))
+    for trans in (0, 1):
+        ct = lib.to_fortran(torch.from_numpy(c))
+        lib.blr_apply_qt(fac, ct, trans=trans)
+        got = ct.cpu().numpy()
+        want = O.apply_qt(fo, c) if trans == 0 else O.apply_q(fo, c)
+        assert np.linalg.norm(got - want) <= 1e-12 * np.linalg.norm(c), trans
+    fac.destroy()
+
+
 def test_residual_and_orthogonality_on_gpu(lib):
     import torch
     m, n, b = 448, 192, 64
